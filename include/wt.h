@@ -1,0 +1,194 @@
+/*
+ * wt.h -- C ABI of the GB300 levelwise wavelet-tree library (libwt.so).
+ *
+ * Construction follows levelWT (Shun, "Parallel Wavelet Tree Construction",
+ * Section 4, Fig. 1): the tree is built one level at a time; on level l every
+ * symbol contributes bit (L-1-l) to the level bitmap and is moved, stably, to
+ * the 0-child or 1-child range of its node for level l+1.  Each level carries
+ * a popcount rank directory (Section 6).  Access, rank and select (defined in
+ * Section 2) are provided as batched device calls for validation.
+ *
+ * Conventions shared by every call:
+ *   - All d_* pointers are device pointers (cudaMalloc'd or equivalent).
+ *     h_* pointers are host pointers (page-locked memory gives the fastest
+ *     copies, pageable memory also works).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream only enqueue work on it and return at once,
+ *     unless stated otherwise.
+ *   - Symbols are unsigned little-endian integers of symbol_bytes = 1, 2 or 4
+ *     bytes; sigma is the alphabet size, 1 <= sigma <= min(2^(8*symbol_bytes), 2^26);
+ *     every symbol must be < sigma.  n < 2^32.
+ *   - L = ceil(log2 sigma) levels (L = 0 when sigma = 1).  Level 0 reads the
+ *     most significant of the L bits ("mask = 2^(L-(l+1))", Fig. 1).
+ *   - Return value: WT_OK (0) or a negative WT_ERR_* code.  Errors detected
+ *     on the host are returned at once and nothing is enqueued.  Errors
+ *     detected by the device (a symbol >= sigma, a wait that timed out) are
+ *     latched in the tree and returned by wt_sync and by later calls on it;
+ *     after WT_ERR_SYMBOL the tree's contents are unspecified.
+ *   - The library never allocates or frees caller memory; every buffer it
+ *     allocates is owned by the tree and released by wt_free.
+ */
+#ifndef WT_H_
+#define WT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WT_OK 0
+#define WT_ERR_ARG (-1)     /* invalid argument (host-side check) */
+#define WT_ERR_OOM (-2)     /* device allocation failed */
+#define WT_ERR_CUDA (-3)    /* a CUDA runtime call failed */
+#define WT_ERR_SYMBOL (-4)  /* the input holds a symbol >= sigma (device-side check) */
+#define WT_ERR_TIMEOUT (-5) /* a bounded device-side wait ran out (device-side check) */
+
+typedef struct wt_tree wt_tree; /* opaque, library-owned */
+
+/*
+ * Output layout, read through wt_info.  All pointers are device pointers
+ * owned by the tree; callers read them and must not free them.
+ *
+ *   d_bits       uint32[L][W], W = words_per_level = 16*ceil(n/512).  Position
+ *                j of level l is bit (j & 31) of d_bits[l*W + (j >> 5)]
+ *                (LSB-first; the paper leaves the bit order open).  Bits past
+ *                n are 0.  Level l holds bit (L-1-l) of the symbols in the
+ *                order T_l of that level (T_0 = S; T_{l+1} is T_l stably
+ *                split, node by node, into 0-children then 1-children).
+ *   d_rank       uint64[L][NB+1], NB = blocks = ceil(n/512).  d_rank[l*(NB+1)+k]
+ *                = number of 1 bits of level l before position 512k (first
+ *                level of the Jacobson directory, Section 6, with 512-bit
+ *                blocks); entry NB is the level's total number of 1 bits.
+ *   d_zeros      uint64[L]: number of 0 bits of each level.
+ *   d_node_start uint64[2^L + 1]: d_node_start[v] = #{j : S[j] < v}.  The
+ *                node of prefix p on level l (Fig. 1's Nodes[2^l - 1 + p])
+ *                starts at d_node_start[p << (L-l)] in that level's bitmap and
+ *                has length d_node_start[(p+1) << (L-l)] - d_node_start[p << (L-l)].
+ */
+typedef struct {
+  uint64_t n;
+  uint32_t sigma;
+  uint32_t symbol_bytes;
+  uint32_t levels;
+  uint32_t reserved;
+  uint64_t words_per_level;
+  uint64_t blocks;
+  uint32_t *d_bits;
+  uint64_t *d_rank;
+  uint64_t *d_zeros;
+  uint64_t *d_node_start;
+} wt_info_t;
+
+/*
+ * Launch configuration.  Zero-initialise and set what you need; zero fields
+ * take the library's choice.
+ *   tile_threads   threads per CTA of the level passes: 128, 256 or 512.  A
+ *                  tile is 32*tile_threads symbols (a multiple of 512).
+ *   ctas_per_sm    cap on resident CTAs per SM for the persistent passes.
+ *   spin_limit     polls before a look-back wait gives up (WT_ERR_TIMEOUT).
+ *   debug_skip_publish
+ *                  test hook: 1 + the tile index (of every pass) that never
+ *                  publishes its look-back status, so that its successor's
+ *                  bounded wait runs out.  0 = off.
+ */
+typedef struct {
+  uint32_t tile_threads;
+  uint32_t ctas_per_sm;
+  uint32_t spin_limit;
+  uint32_t debug_skip_publish;
+} wt_config;
+
+/*
+ * Allocate a tree for sequences of n symbols over [0, sigma) stored in
+ * symbol_bytes bytes each.  Allocates device memory (cudaMalloc) for the
+ * outputs and for scratch: two ping-pong buffers of n*symbol_bytes bytes
+ * (rounded up to whole tiles), a 2^L-bin histogram, per-level tables and the
+ * look-back state.  No kernel runs.  cfg may be NULL.
+ * Errors: WT_ERR_ARG, WT_ERR_OOM, WT_ERR_CUDA.
+ */
+int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+              wt_tree **out);
+
+/*
+ * Enqueue the construction of `tree` from d_seq[0..n) on `stream` (levelWT,
+ * Fig. 1): a pre-pass that histograms the symbols and writes level 0's bits
+ * and directory, the node tables, one split pass per level l = 0..L-2
+ * (bits, directory and the stable split into T_{l+1}), and a last pass for
+ * level L-1.  Every size is known on the host, so the call has no host
+ * synchronisation and may be captured into a CUDA graph.
+ * d_seq is read-only; it must stay valid until the stream work completes.
+ * A d_seq that is not 16-byte aligned is first copied into tree scratch.
+ * Errors: WT_ERR_ARG, WT_ERR_CUDA; device errors are reported by wt_sync.
+ */
+int wt_rebuild(wt_tree *tree, const void *d_seq, void *stream);
+
+/* wt_create followed by wt_rebuild. */
+int wt_build(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+             void *stream, wt_tree **out);
+
+/* Same, with a launch configuration (may be NULL). */
+int wt_build_ex(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                const wt_config *cfg, void *stream, wt_tree **out);
+
+/*
+ * Host-memory path: copy h_seq[0..n) to the device, build, and copy the
+ * bitmaps (L*W uint32) into h_bits and the directory (L*(NB+1) uint64) into
+ * h_rank (either may be NULL to skip that copy).  Synchronises `stream`
+ * before returning and returns the build status (as wt_sync).
+ * The tree must have been created for this n, sigma and symbol_bytes.
+ */
+int wt_build_host(wt_tree *tree, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
+                  void *stream);
+
+/* Wait for the tree's last enqueued work and return its status. */
+int wt_sync(wt_tree *tree);
+
+/* Describe the tree's outputs (see wt_info_t).  Does not synchronise. */
+int wt_info(const wt_tree *tree, wt_info_t *info);
+
+/*
+ * Batched queries over a built tree (Section 2 definitions), one result per
+ * query, enqueued on `stream`.  The tree's build must be complete in stream
+ * order (same stream, or synchronised).  Queries walk the levels with rank on
+ * the bitmaps; node ranges are derived by rank, so the node table is not used.
+ *   wt_access: d_out[q] = S[d_i[q]]; UINT32_MAX when d_i[q] >= n.
+ *   wt_rank:   d_out[q] = #{j <= d_i[q] : S[j] = d_c[q]} (inclusive);
+ *              UINT64_MAX when d_i[q] >= n or d_c[q] >= sigma.
+ *   wt_select: d_out[q] = position of the d_k[q]-th occurrence of d_c[q]
+ *              (k counted from 1), so that select_c(rank_c(i)) = i when
+ *              S[i] = c; UINT64_MAX when k = 0, k exceeds the number of
+ *              occurrences, or d_c[q] >= sigma.
+ * m = 0 is valid and does nothing.  Errors: WT_ERR_ARG, WT_ERR_CUDA.
+ */
+int wt_access(const wt_tree *tree, const uint64_t *d_i, uint64_t m, uint32_t *d_out,
+              void *stream);
+int wt_rank(const wt_tree *tree, const uint32_t *d_c, const uint64_t *d_i, uint64_t m,
+            uint64_t *d_out, void *stream);
+int wt_select(const wt_tree *tree, const uint32_t *d_c, const uint64_t *d_k, uint64_t m,
+              uint64_t *d_out, void *stream);
+
+/*
+ * Per-kernel timing of the following builds of `tree` (measurement support).
+ * wt_profile(tree, 1) starts a recording window: every later wt_rebuild
+ * records a CUDA event pair on its stream around each kernel it launches (up
+ * to 2048 launches per window).  wt_profile_read, after wt_sync, returns the
+ * number of launches recorded in the window and fills up to `cap` entries of
+ * ms[] with each launch's duration and kind[] with its kind: 0 pre-pass,
+ * 1 histogram scan, 2 node tables, 3 split pass, 4 last-level pass.
+ * wt_profile(tree, 0) stops recording.
+ */
+int wt_profile(wt_tree *tree, int enable);
+int wt_profile_read(wt_tree *tree, float *ms, int32_t *kind, int32_t cap);
+
+/* Release everything the tree owns.  Synchronises the tree's last stream. */
+int wt_free(wt_tree *tree);
+
+/* Number of kernels one wt_rebuild of this tree launches. */
+int wt_kernels_per_build(const wt_tree *tree);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WT_H_ */

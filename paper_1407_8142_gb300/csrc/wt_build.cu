@@ -1,0 +1,934 @@
+// levelWT construction on one GB300 (sm_103a).
+//
+// One build (Shun, "Parallel Wavelet Tree Construction", Section 4, Fig. 1,
+// restated as global passes over each level's sequence T_l):
+//   pre-pass   reads S once: level-0 bits (bit L-1 of every symbol), level-0
+//              rank directory, the 2^L-bin symbol histogram, the range check.
+//   tables     node starts E[v] = #{S[j] < v} by an exclusive scan of the
+//              histogram; per level l and node prefix p the ones before the
+//              node, O_l[p], and the start of its 1-child.  These replace the
+//              per-node prefix-sum totals X_s and the node list A of Fig. 1.
+//   split(l)   l = 0..L-2: bits and directory of level l (l >= 1), the
+//              ones-before-tile prefix by single-pass decoupled look-back, and
+//              the stable split of every node into its 0-child and 1-child
+//              ranges of T_{l+1} (Fig. 1's X_s + i - X[i] placement, with the
+//              prefix sum taken over the whole level instead of per node).
+//   leaf       level L-1: bits and directory only; its nodes have range 2 and
+//              no children (the early stop of Fig. 1).
+//
+// Destinations.  For symbol s at position j of T_l, with node prefix
+// p = s >> (L-l), bit beta = bit (L-1-l) of s and R(j) = ones of level l
+// before j:  beta = 0 -> j - R(j) + O_l[p];  beta = 1 -> E_{l+1}[2p+1] +
+// R(j) - O_l[p].  The tables store {O_l[p], E_{l+1}[2p+1] - O_l[p]}.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "wt_dev.cuh"
+#include "wt_internal.h"
+
+using namespace wtk;
+
+namespace {
+
+constexpr uint32_t kHistSmemMaxBins = 8192;
+constexpr uint32_t kScanThreads = 256;
+constexpr uint32_t kScanItems = 8;
+constexpr uint32_t kScanChunk = kScanThreads * kScanItems;
+constexpr uint32_t kDefaultSpin = 1u << 22;
+
+// ------------------------------------------------------------------ bits pass
+struct BitsArgs {
+  const uint8_t *in;  // this level's symbols T_l (16-byte aligned)
+  uint32_t n, L, level, NT, NB;
+  uint64_t W;
+  uint32_t *bits;              // level's bitmap
+  unsigned long long *rank;    // level's directory, NB+1 entries
+  unsigned long long *zeros;   // &zeros[level]
+  uint32_t *ticket;
+  Lookback lb;
+  uint32_t *hist;  // pre-pass only
+  uint32_t sigma;  // pre-pass only
+};
+
+template <int SB>
+__device__ __forceinline__ void load32(const uint8_t *g, uint32_t my0, uint32_t nv, uint32_t *u) {
+  if (my0 + 32 <= nv) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(g);
+#pragma unroll
+    for (int c = 0; c < 2 * SB; ++c) {
+      const uint4 v = __ldg(src + c);
+      u[4 * c + 0] = v.x;
+      u[4 * c + 1] = v.y;
+      u[4 * c + 2] = v.z;
+      u[4 * c + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8 * SB; ++i) u[i] = 0;
+    for (uint32_t q = 0; q < 32 && my0 + q < nv; ++q) {
+      uint32_t s;
+      if (SB == 1) s = g[q];
+      else if (SB == 2) s = reinterpret_cast<const uint16_t *>(g)[q];
+      else s = reinterpret_cast<const uint32_t *>(g)[q];
+      if (SB == 1) u[q >> 2] |= s << (8 * (q & 3));
+      else if (SB == 2) u[q >> 1] |= s << (16 * (q & 1));
+      else u[q] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t valid_mask(uint32_t my0, uint32_t nv) {
+  if (my0 + 32 <= nv) return 0xFFFFFFFFu;
+  if (my0 >= nv) return 0u;
+  return (1u << (nv - my0)) - 1u;
+}
+
+// Pre-pass (PREPASS = true: level 0 of S plus histogram and range check) and
+// the last level (PREPASS = false).  Persistent CTAs take tiles in ticket
+// order, so a tile only ever waits on tiles already held by running CTAs.
+template <int SB, int THREADS, bool PREPASS, bool HIST_SMEM>
+__global__ void __launch_bounds__(THREADS) k_bits(BitsArgs a) {
+  constexpr uint32_t T = 32 * THREADS;
+  extern __shared__ __align__(16) uint32_t s_hist[];
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_tile, s_R;
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  const uint32_t k = a.L ? a.L - 1 - a.level : 0u;  // L = 0: no bits, check + histogram only
+  const uint32_t lmask = (1u << a.L) - 1u;
+  const uint32_t nbins = 1u << a.L;
+  uint32_t bad = 0;
+  if (PREPASS && HIST_SMEM)
+    for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
+
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= a.NT) break;
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    const uint32_t my0 = 32 * tid;
+    uint32_t u[8 * SB];
+    load32<SB>(a.in + (start + my0) * SB, my0, nv, u);
+    const uint32_t word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
+    if (PREPASS) {
+#pragma unroll 4
+      for (int q = 0; q < 32; ++q) {
+        const bool valid = my0 + q < nv;
+        const uint32_t s = symbol_at<SB>(u, q);
+        if (valid) bad |= (uint32_t)(s >= a.sigma);
+        if (HIST_SMEM) {
+          if (valid) atomicAdd(&s_hist[s & lmask], 1u);
+        } else {
+          const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
+          if (valid) {
+            const uint32_t v = s & lmask;
+            const uint32_t peers = __match_any_sync(am, v);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
+          }
+        }
+      }
+    }
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
+    if (tid < 32) {
+      const uint32_t R = lookback(a.lb, tile, 0, total);
+      if (tid == 0) s_R = R;
+    }
+    __syncthreads();
+    const uint32_t R = s_R;
+    const uint64_t widx = (uint64_t)tile * THREADS + tid;
+    if (widx < a.W) a.bits[widx] = word;
+    if ((tid & 15) == 0 && start + my0 < a.n) a.rank[(start + my0) >> 9] = R + excl;
+    if (tile == a.NT - 1 && tid == 0) {
+      a.rank[a.NB] = R + total;
+      *a.zeros = (unsigned long long)(a.n - (R + total));
+    }
+  }
+  if (PREPASS) {
+    if (bad) latch_error(a.lb.err, WT_ERR_SYMBOL);
+    if (HIST_SMEM) {
+      __syncthreads();
+      for (uint32_t i = tid; i < nbins; i += THREADS)
+        if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ split pass
+struct SplitArgs {
+  const uint8_t *in;   // T_l, 16-byte aligned
+  uint8_t *out;        // T_{l+1}
+  int in_padded;       // in holds whole tiles (scratch buffer) -> copy full tiles
+  uint32_t n, L, level, NT, NB;
+  uint64_t W;
+  const uint2 *tab;    // this level's {O_l[p], E_{l+1}[2p+1] - O_l[p]}
+  uint32_t *bits;      // level's bitmap, or nullptr when already written
+  unsigned long long *rank;
+  unsigned long long *zeros;
+  const unsigned long long *rank_known;  // level's directory when already built (level 0)
+  uint32_t *ticket;
+  Lookback lb;
+};
+
+// Copy `len` bytes from shared memory (byte offset soff of a 16-byte aligned
+// array) to global gout[goff..): unaligned head and tail bytes singly, the
+// body as aligned 16-byte stores.  Writes past gbound are dropped (only
+// reachable after a device error).
+template <int THREADS>
+__device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, uint8_t *gout,
+                                         uint64_t goff, uint32_t len, uint64_t gbound) {
+  if (goff >= gbound) return;
+  if (goff + len > gbound) len = (uint32_t)(gbound - goff);
+  if (len == 0) return;
+  uint8_t *dst = gout + goff;
+  const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbase);
+  const uint32_t mis = (uint32_t)(reinterpret_cast<uintptr_t>(dst) & 15u);
+  const uint32_t head = min(len, (16u - mis) & 15u);
+  const uint32_t nch = (len - head) >> 4;
+  const uint32_t tail0 = head + (nch << 4);
+  const uint32_t tail = len - tail0;
+  const uint32_t t = threadIdx.x;
+  if (t < head) {
+    dst[t] = sb[soff + t];
+  } else if (t < head + tail) {
+    const uint32_t o = tail0 + (t - head);
+    dst[o] = sb[soff + o];
+  }
+  for (uint32_t c = t; c < nch; c += THREADS) {
+    const uint32_t o = head + (c << 4);
+    *reinterpret_cast<uint4 *>(dst + o) = lds16_unaligned(sbase, soff + o);
+  }
+}
+
+template <int SB>
+struct SymT;
+template <>
+struct SymT<1> { using type = uint8_t; };
+template <>
+struct SymT<2> { using type = uint16_t; };
+template <>
+struct SymT<4> { using type = uint32_t; };
+
+template <int SB, int THREADS>
+constexpr uint32_t split_smem_bytes() {
+  // two input tiles, one output tile (+16 bytes of slack for unaligned reads),
+  // per-thread bit words and ones-prefixes, two mbarriers
+  return 3u * 32u * THREADS * SB + 16u + 8u * THREADS + 16u;
+}
+
+template <int SB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
+  using Sym = typename SymT<SB>::type;
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t TB = T * SB;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t *const sIn0 = smem;
+  uint8_t *const sIn1 = smem + TB;
+  uint8_t *const sOut = smem + 2 * TB;
+  uint32_t *const sWord = reinterpret_cast<uint32_t *>(smem + 3 * TB + 16);
+  uint32_t *const sPref = sWord + THREADS;
+  uint64_t *const bar = reinterpret_cast<uint64_t *>(sPref + THREADS);
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_ticket[2];
+  __shared__ uint32_t s_R;
+
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t k = a.L - 1 - a.level;
+  const uint32_t pshift = a.L - a.level;
+  const uint32_t lmask = (1u << a.L) - 1u;
+  const uint32_t spin = a.lb.spin_limit;
+
+  auto issue = [&](uint32_t tile, int buf) {
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    const uint32_t bytes = a.in_padded ? TB : ((nv * SB) & ~15u);
+    mbar_arrive_expect_tx(&bar[buf], bytes);
+    if (bytes) bulk_g2s(buf ? sIn1 : sIn0, a.in + start * SB, bytes, &bar[buf]);
+  };
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    const uint32_t t0 = atomicAdd(a.ticket, 1u);
+    s_ticket[0] = t0;
+    if (t0 < a.NT) issue(t0, 0);
+  }
+  __syncthreads();
+
+  for (uint32_t it = 0;; ++it) {
+    const int buf = it & 1;
+    const uint32_t tile = s_ticket[buf];
+    if (tile >= a.NT) break;
+    uint8_t *const sIn = buf ? sIn1 : sIn0;
+    if (tid == 0) {
+      const uint32_t nx = atomicAdd(a.ticket, 1u);
+      s_ticket[buf ^ 1] = nx;
+      if (nx < a.NT) {
+        fence_proxy_async_smem();
+        issue(nx, buf ^ 1);
+      }
+    }
+    const bool ok = mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, spin, a.lb.err);
+    if (__syncthreads_or(!ok)) {
+      // The copy did not land in time: wait once more (bounded) for the
+      // copies this CTA started, then stop.
+      if (tid == 0) {
+        mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, spin, a.lb.err);
+        mbar_wait_bounded(&bar[buf ^ 1], ((it + 1) >> 1) & 1u, spin, a.lb.err);
+      }
+      __syncthreads();
+      return;
+    }
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    if (!a.in_padded && ((nv * SB) & 15u)) {  // tail bytes of an unpadded input
+      for (uint32_t i = ((nv * SB) & ~15u) + tid; i < nv * SB; i += THREADS)
+        sIn[i] = a.in[start * SB + i];
+      __syncthreads();
+    }
+
+    // Pass A: 32 consecutive symbols per thread -> one bitmap word.
+    const uint32_t my0 = 32 * tid;
+    uint32_t u[8 * SB];
+    {
+      const uint4 *src = reinterpret_cast<const uint4 *>(sIn + my0 * SB);
+#pragma unroll
+      for (int c = 0; c < 2 * SB; ++c) {
+        const uint4 v = src[c];
+        u[4 * c + 0] = v.x;
+        u[4 * c + 1] = v.y;
+        u[4 * c + 2] = v.z;
+        u[4 * c + 3] = v.w;
+      }
+    }
+    const uint32_t word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
+    sWord[tid] = word;
+    sPref[tid] = excl;
+    if (a.rank_known) {
+      // level 0: the pre-pass already holds R(tile start) in its directory
+      if (tid == 0) s_R = (uint32_t)a.rank_known[start >> 9];
+    } else if (warp == 0) {
+      const uint32_t R = lookback(a.lb, tile, 0, total);
+      if (lane == 0) s_R = R;
+    }
+    __syncthreads();
+    const uint32_t R = s_R;
+    if (a.bits) {
+      const uint64_t widx = (uint64_t)tile * THREADS + tid;
+      if (widx < a.W) a.bits[widx] = word;
+      if ((tid & 15) == 0 && start + my0 < a.n) a.rank[(start + my0) >> 9] = R + excl;
+      if (tile == a.NT - 1 && tid == 0) {
+        a.rank[a.NB] = R + total;
+        *a.zeros = (unsigned long long)(a.n - (R + total));
+      }
+    }
+
+    // Pass B: stable split of the tile into shared memory, zeros first.
+    // Warp w owns tile positions [1024w, 1024w + 1024); step q covers the
+    // 32 positions of bitmap word 32w + q, one per lane.
+    const uint32_t Zt = nv - total;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t seg = 1024 * warp;
+    const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
+    Sym *sOutS = reinterpret_cast<Sym *>(sOut);
+    if (seg + 1024 <= nv) {
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) {
+        const uint32_t pos = seg + 32 * q + lane;
+        const uint32_t B = sWord[32 * warp + q];
+        const uint32_t P = sPref[32 * warp + q];
+        const Sym s = sInS[pos];
+        const uint32_t r = P + __popc(B & lt);
+        const uint32_t dst = ((B >> lane) & 1u) ? Zt + r : pos - r;
+        sOutS[dst] = s;
+      }
+    } else if (seg < nv) {
+      for (int q = 0; q < 32; ++q) {
+        const uint32_t pos = seg + 32 * q + lane;
+        if (pos < nv) {
+          const uint32_t B = sWord[32 * warp + q];
+          const uint32_t P = sPref[32 * warp + q];
+          const Sym s = sInS[pos];
+          const uint32_t r = P + __popc(B & lt);
+          const uint32_t dst = ((B >> lane) & 1u) ? Zt + r : pos - r;
+          sOutS[dst] = s;
+        }
+      }
+    }
+    __syncthreads();
+
+    // Phase 2: write the tile's runs to T_{l+1}.
+    const uint32_t Zb = (uint32_t)start - R;  // zeros of level l before the tile
+    const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
+    const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
+    const uint64_t gbound = (uint64_t)a.n * SB;
+    if (pf == pl) {
+      // the whole tile lies in one node: one run of zeros, one run of ones
+      const uint2 tb = __ldg(&a.tab[pf]);
+      const uint32_t *sO = reinterpret_cast<const uint32_t *>(sOut);
+      copy_run<THREADS>(sO, 0, a.out, (uint64_t)(tb.x + Zb) * SB, Zt * SB, gbound);
+      copy_run<THREADS>(sO, Zt * SB, a.out, (uint64_t)(tb.y + R) * SB, (nv - Zt) * SB, gbound);
+    } else {
+      Sym *outS = reinterpret_cast<Sym *>(a.out);
+      for (uint32_t kk = tid; kk < nv; kk += THREADS) {
+        const Sym s = sOutS[kk];
+        const uint32_t p = ((uint32_t)s & lmask) >> pshift;
+        const uint2 tb = __ldg(&a.tab[p]);
+        const uint32_t dest = kk < Zt ? tb.x + Zb + kk : tb.y + R + (kk - Zt);
+        if (dest < a.n) outS[dest] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ tables
+struct ScanArgs {
+  const uint32_t *hist;
+  unsigned long long *E;  // 2^L + 1 entries
+  uint32_t nbins, nblocks;
+  uint32_t *ticket;
+  Lookback lb;
+};
+
+// E[v] = sum of hist[0..v), E[nbins] = total.
+__global__ void __launch_bounds__(kScanThreads) k_hist_scan(ScanArgs a) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_tile, s_P;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= a.nblocks) return;
+  const uint32_t base = tile * kScanChunk + tid * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    v[i] = base + i < a.nbins ? a.hist[base + i] : 0u;
+    sum += v[i];
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<kScanThreads>(sum, s_warp, &total);
+  if (tid < 32) {
+    const uint32_t P = lookback(a.lb, tile, 0, total);
+    if (tid == 0) s_P = P;
+  }
+  __syncthreads();
+  uint32_t run = s_P + excl;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    if (base + i < a.nbins) a.E[base + i] = run;
+    run += v[i];
+  }
+  if (tile == a.nblocks - 1 && tid == 0) a.E[a.nbins] = s_P + total;
+}
+
+struct TabArgs {
+  const unsigned long long *E;
+  uint2 *tab;
+  uint32_t L, nblocks;
+  uint32_t *ticket;
+  Lookback lb;
+};
+
+// For levels l = 0..L-2 and prefixes p < 2^l:
+//   c1(p) = E[(2p+2) << (L-l-1)] - E[(2p+1) << (L-l-1)]   (size of node 2p+1 on level l+1)
+//   O_l(p) = sum of c1 over prefixes < p                     (ones of level l before node p)
+//   tab[2^l - 1 + p] = {O_l(p), E[(2p+1) << (L-l-1)] - O_l(p)}
+// Blocks are numbered level by level; each level is one look-back segment.
+__global__ void __launch_bounds__(kScanThreads) k_level_tables(TabArgs a) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_tile, s_P;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= a.nblocks) return;
+  uint32_t l = 0, first = 0;
+  for (; l + 1 < a.L; ++l) {
+    const uint32_t nb = ((1u << l) + kScanChunk - 1) / kScanChunk;
+    if (tile < first + nb) break;
+    first += nb;
+  }
+  const uint32_t cnt = 1u << l;
+  const uint32_t sh = a.L - l - 1;
+  const uint32_t base = (tile - first) * kScanChunk + tid * kScanItems;
+  uint32_t c1[kScanItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    const uint32_t p = base + i;
+    c1[i] = p < cnt ? (uint32_t)(a.E[(uint64_t)(2 * p + 2) << sh] - a.E[(uint64_t)(2 * p + 1) << sh])
+                    : 0u;
+    sum += c1[i];
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<kScanThreads>(sum, s_warp, &total);
+  if (tid < 32) {
+    const uint32_t P = lookback(a.lb, tile, first, total);
+    if (tid == 0) s_P = P;
+  }
+  __syncthreads();
+  uint32_t O = s_P + excl;
+  uint2 *tl = a.tab + (cnt - 1);
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    const uint32_t p = base + i;
+    if (p < cnt) tl[p] = make_uint2(O, (uint32_t)a.E[(uint64_t)(2 * p + 1) << sh] - O);
+    O += c1[i];
+  }
+}
+
+// ------------------------------------------------------------------ host side
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return WT_ERR_OOM;
+  return WT_ERR_CUDA;
+}
+
+#define WT_CUDA(call)                         \
+  do {                                        \
+    cudaError_t e__ = (call);                 \
+    if (e__ != cudaSuccess) {                 \
+      (void)cudaGetLastError();               \
+      return cuda_fail(e__);                  \
+    }                                         \
+  } while (0)
+
+uint32_t levels_of(uint32_t sigma) {
+  uint32_t L = 0;
+  while ((1ull << L) < sigma) ++L;
+  return L;
+}
+
+uint32_t tables_blocks(uint32_t L) {
+  uint32_t nb = 0;
+  for (uint32_t l = 0; l + 1 < L; ++l) nb += ((1u << l) + kScanChunk - 1) / kScanChunk;
+  return nb;
+}
+
+uint32_t hist_blocks(uint32_t L) { return ((1u << L) + kScanChunk - 1) / kScanChunk; }
+
+template <typename K>
+int occupancy(K kernel, int threads, size_t smem, int sms, uint32_t cap) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    occ = 1;
+  }
+  occ = std::max(occ, 1);
+  if (cap) occ = std::min<int>(occ, (int)cap);
+  return occ * sms;
+}
+
+struct Launcher {
+  wt_tree *t;
+  cudaStream_t st;
+  uint32_t epoch_base;
+  uint32_t pass = 0;
+
+  Lookback lb() const {
+    Lookback l;
+    l.status = t->d_status;
+    l.epoch = epoch_base + pass;
+    l.spin_limit = t->cfg.spin_limit ? t->cfg.spin_limit : kDefaultSpin;
+    l.skip = t->cfg.debug_skip_publish;
+    l.err = reinterpret_cast<int *>(t->d_ctrl + kCtrlErr);
+    return l;
+  }
+  uint32_t *ticket() const { return t->d_ctrl + pass; }
+
+  void before(int kind) {
+    if (t->profile && t->n_ev < (int)kMaxProfiled) {
+      cudaEventRecord(t->ev[2 * t->n_ev], st);
+      t->ev_kind[t->n_ev] = kind;
+    }
+  }
+  void after() {
+    if (t->profile && t->n_ev < (int)kMaxProfiled) {
+      cudaEventRecord(t->ev[2 * t->n_ev + 1], st);
+      ++t->n_ev;
+    }
+  }
+};
+
+template <int SB, int THREADS>
+int launch_bits(Launcher &ln, const uint8_t *in, uint32_t level, bool prepass) {
+  wt_tree *t = ln.t;
+  BitsArgs a;
+  a.in = in;
+  a.n = (uint32_t)t->n;
+  a.L = t->L;
+  a.level = level;
+  a.NT = (uint32_t)t->NT;
+  a.NB = (uint32_t)t->NB;
+  a.W = t->W;
+  a.bits = t->d_bits + (uint64_t)level * t->W;
+  a.rank = t->d_rank + (uint64_t)level * (t->NB + 1);
+  a.zeros = t->d_zeros + level;
+  a.ticket = ln.ticket();
+  a.lb = ln.lb();
+  a.hist = t->d_hist;
+  a.sigma = t->sigma;
+  const uint32_t nbins = 1u << t->L;
+  ln.before(prepass ? kPrepass : kLeaf);
+  if (prepass && nbins <= kHistSmemMaxBins) {
+    auto kern = k_bits<SB, THREADS, true, true>;
+    const size_t sm = nbins * sizeof(uint32_t);
+    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
+    kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
+  } else if (prepass) {
+    auto kern = k_bits<SB, THREADS, true, false>;
+    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, 0, t->sms, t->cfg.ctas_per_sm));
+    kern<<<std::max(grid, 1), THREADS, 0, ln.st>>>(a);
+  } else {
+    auto kern = k_bits<SB, THREADS, false, false>;
+    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, 0, t->sms, t->cfg.ctas_per_sm));
+    kern<<<std::max(grid, 1), THREADS, 0, ln.st>>>(a);
+  }
+  ln.after();
+  ++ln.pass;
+  WT_CUDA(cudaGetLastError());
+  return WT_OK;
+}
+
+template <int SB, int THREADS>
+int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, uint32_t level) {
+  wt_tree *t = ln.t;
+  SplitArgs a;
+  a.in = in;
+  a.out = out;
+  a.in_padded = in_padded ? 1 : 0;
+  a.n = (uint32_t)t->n;
+  a.L = t->L;
+  a.level = level;
+  a.NT = (uint32_t)t->NT;
+  a.NB = (uint32_t)t->NB;
+  a.W = t->W;
+  a.tab = t->d_tab + ((1u << level) - 1);
+  a.bits = level ? t->d_bits + (uint64_t)level * t->W : nullptr;
+  a.rank = t->d_rank + (uint64_t)level * (t->NB + 1);
+  a.zeros = t->d_zeros + level;
+  a.rank_known = level ? nullptr : t->d_rank;
+  a.ticket = ln.ticket();
+  a.lb = ln.lb();
+  auto kern = k_split<SB, THREADS>;
+  constexpr uint32_t sm = split_smem_bytes<SB, THREADS>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    WT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set = true;
+  }
+  const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
+  ln.before(kSplit);
+  kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
+  ln.after();
+  ++ln.pass;
+  WT_CUDA(cudaGetLastError());
+  return WT_OK;
+}
+
+int launch_tables(Launcher &ln) {
+  wt_tree *t = ln.t;
+  {
+    ScanArgs a;
+    a.hist = t->d_hist;
+    a.E = t->d_node_start;
+    a.nbins = 1u << t->L;
+    a.nblocks = hist_blocks(t->L);
+    a.ticket = ln.ticket();
+    a.lb = ln.lb();
+    ln.before(kHistScan);
+    k_hist_scan<<<a.nblocks, kScanThreads, 0, ln.st>>>(a);
+    ln.after();
+    ++ln.pass;
+    WT_CUDA(cudaGetLastError());
+  }
+  const uint32_t nb = tables_blocks(t->L);
+  if (nb) {
+    TabArgs a;
+    a.E = t->d_node_start;
+    a.tab = t->d_tab;
+    a.L = t->L;
+    a.nblocks = nb;
+    a.ticket = ln.ticket();
+    a.lb = ln.lb();
+    ln.before(kTables);
+    k_level_tables<<<nb, kScanThreads, 0, ln.st>>>(a);
+    ln.after();
+    WT_CUDA(cudaGetLastError());
+  }
+  ++ln.pass;
+  return WT_OK;
+}
+
+template <int SB, int THREADS>
+int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
+  Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
+  int rc;
+  if ((rc = launch_bits<SB, THREADS>(ln, seq, 0, true))) return rc;
+  if ((rc = launch_tables(ln))) return rc;
+  if (t->L < 2) return WT_OK;
+  const uint8_t *in = seq;
+  bool padded = seq_padded;
+  for (uint32_t l = 0; l + 1 < t->L; ++l) {
+    uint8_t *out = static_cast<uint8_t *>(t->d_buf[l & 1]);
+    if ((rc = launch_split<SB, THREADS>(ln, in, padded, out, l))) return rc;
+    in = out;
+    padded = true;
+  }
+  return launch_bits<SB, THREADS>(ln, in, t->L - 1, false);
+}
+
+template <int SB>
+int run_build_sb(wt_tree *t, const uint8_t *seq, bool padded, cudaStream_t st) {
+  switch (t->threads) {
+    case 128: return run_build<SB, 128>(t, seq, padded, st);
+    case 256: return run_build<SB, 256>(t, seq, padded, st);
+    case 512: return run_build<SB, 512>(t, seq, padded, st);
+  }
+  return WT_ERR_ARG;
+}
+
+void release(wt_tree *t) {
+  cudaFree(t->d_bits);
+  cudaFree(t->d_rank);
+  cudaFree(t->d_zeros);
+  cudaFree(t->d_node_start);
+  cudaFree(t->d_tab);
+  cudaFree(t->d_ctrl);
+  cudaFree(t->d_buf[0]);
+  cudaFree(t->d_buf[1]);
+  cudaFree(t->d_status);
+  cudaFree(t->d_in_host);
+  if (t->ev) {
+    for (uint32_t i = 0; i < 2 * kMaxProfiled; ++i)
+      if (t->ev[i]) cudaEventDestroy(t->ev[i]);
+    delete[] t->ev;
+    delete[] t->ev_kind;
+  }
+}
+
+uint32_t pick_threads(uint64_t n, uint32_t sb, int sms, uint32_t requested) {
+  if (requested == 128 || requested == 256 || requested == 512) return requested;
+  // the largest tile that still gives every SM two tiles; 128 threads below that
+  for (uint32_t th : {512u, 256u}) {
+    if (sb == 4 && th == 512) continue;  // 64 KB tiles leave one CTA per SM
+    if ((n + 32ull * th - 1) / (32ull * th) >= 2ull * (uint64_t)sms) return th;
+  }
+  return 128;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+              wt_tree **out) {
+  if (!out) return WT_ERR_ARG;
+  *out = nullptr;
+  if (!(symbol_bytes == 1 || symbol_bytes == 2 || symbol_bytes == 4)) return WT_ERR_ARG;
+  if (sigma == 0 || (uint64_t)sigma > (1ull << (8 * symbol_bytes))) return WT_ERR_ARG;
+  if (n >= (1ull << 32)) return WT_ERR_ARG;
+  const uint32_t L = levels_of(sigma);
+  if (L > kMaxLevels) return WT_ERR_ARG;
+  if (cfg && cfg->tile_threads && !(cfg->tile_threads == 128 || cfg->tile_threads == 256 ||
+                                    cfg->tile_threads == 512))
+    return WT_ERR_ARG;
+
+  wt_tree *t = new (std::nothrow) wt_tree();
+  if (!t) return WT_ERR_OOM;
+  if (cfg) t->cfg = *cfg;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete t;
+    return WT_ERR_CUDA;
+  }
+  t->n = n;
+  t->sigma = sigma;
+  t->sb = symbol_bytes;
+  t->L = L;
+  t->NB = (n + 511) / 512;
+  t->W = 16 * t->NB;
+  t->threads = pick_threads(n, symbol_bytes, t->sms, t->cfg.tile_threads);
+  t->T = 32ull * t->threads;
+  t->NT = std::max<uint64_t>(1, (n + t->T - 1) / t->T);
+
+  auto fail = [&](cudaError_t e) {
+    (void)cudaGetLastError();
+    release(t);
+    delete t;
+    return cuda_fail(e);
+  };
+  cudaError_t e;
+  const uint64_t nbins = 1ull << L;
+  const size_t Lz = std::max<uint32_t>(L, 1);
+  if ((e = cudaMalloc(&t->d_bits, std::max<size_t>(4, Lz * t->W * 4)))) return fail(e);
+  if ((e = cudaMalloc(&t->d_rank, Lz * (t->NB + 1) * 8))) return fail(e);
+  if ((e = cudaMalloc(&t->d_zeros, Lz * 8))) return fail(e);
+  if ((e = cudaMalloc(&t->d_node_start, (nbins + 1) * 8))) return fail(e);
+  if ((e = cudaMalloc(&t->d_tab, std::max<uint64_t>(1, nbins / 2) * sizeof(uint2)))) return fail(e);
+  if ((e = cudaMalloc(&t->d_ctrl, (kCtrlWords + nbins) * 4))) return fail(e);
+  t->d_hist = t->d_ctrl + kCtrlWords;
+  t->buf_bytes = t->NT * t->T * symbol_bytes + 16;
+  if (L >= 2) {
+    if ((e = cudaMalloc(&t->d_buf[0], t->buf_bytes))) return fail(e);
+    if ((e = cudaMalloc(&t->d_buf[1], t->buf_bytes))) return fail(e);
+  }
+  t->status_n = std::max<uint64_t>({t->NT, (uint64_t)hist_blocks(L), (uint64_t)tables_blocks(L), 1});
+  if ((e = cudaMalloc(&t->d_status, t->status_n * 8))) return fail(e);
+  if ((e = cudaMemset(t->d_status, 0, t->status_n * 8))) return fail(e);
+  if ((e = cudaMemset(t->d_zeros, 0, Lz * 8))) return fail(e);
+  if ((e = cudaMemset(t->d_rank, 0, Lz * (t->NB + 1) * 8))) return fail(e);
+  *out = t;
+  return WT_OK;
+}
+
+int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
+  if (!t || (!d_seq && t->n)) return WT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  t->stream = st;
+  t->sticky_error = 0;
+  ++t->build_count;
+  const uint64_t nbins = 1ull << t->L;
+  WT_CUDA(cudaMemsetAsync(t->d_ctrl, 0, (kCtrlWords + nbins) * 4, st));
+  const uint8_t *seq = static_cast<const uint8_t *>(d_seq);
+  bool padded = false;
+  if (t->n && (reinterpret_cast<uintptr_t>(seq) & 15u)) {
+    // TMA and vector loads need 16-byte alignment: stage the input.
+    void *dst = t->L >= 2 ? t->d_buf[1] : nullptr;
+    if (!dst) {
+      if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->NT * t->T * t->sb + 16));
+      dst = t->d_in_host;
+    }
+    WT_CUDA(cudaMemcpyAsync(dst, seq, t->n * t->sb, cudaMemcpyDeviceToDevice, st));
+    seq = static_cast<const uint8_t *>(dst);
+  }
+  if (t->n == 0) {
+    // nothing to scan: zero bits/directories are already in place; node
+    // starts are all zero
+    WT_CUDA(cudaMemsetAsync(t->d_node_start, 0, (nbins + 1) * 8, st));
+    return WT_OK;
+  }
+  switch (t->sb) {
+    case 1: return run_build_sb<1>(t, seq, padded, st);
+    case 2: return run_build_sb<2>(t, seq, padded, st);
+    case 4: return run_build_sb<4>(t, seq, padded, st);
+  }
+  return WT_ERR_ARG;
+}
+
+int wt_build_ex(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                const wt_config *cfg, void *stream, wt_tree **out) {
+  int rc = wt_create(n, sigma, symbol_bytes, cfg, out);
+  if (rc) return rc;
+  rc = wt_rebuild(*out, d_seq, stream);
+  if (rc) {
+    wt_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int wt_build(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes, void *stream,
+             wt_tree **out) {
+  return wt_build_ex(d_seq, n, sigma, symbol_bytes, nullptr, stream, out);
+}
+
+int wt_sync(wt_tree *t) {
+  if (!t) return WT_ERR_ARG;
+  WT_CUDA(cudaStreamSynchronize(t->stream));
+  int err = 0;
+  WT_CUDA(cudaMemcpy(&err, t->d_ctrl + kCtrlErr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) t->sticky_error = err;
+  return t->sticky_error;
+}
+
+int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
+                  void *stream) {
+  if (!t || (!h_seq && t->n)) return WT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->NT * t->T * t->sb + 16));
+  if (t->n) WT_CUDA(cudaMemcpyAsync(t->d_in_host, h_seq, t->n * t->sb, cudaMemcpyHostToDevice, st));
+  int rc = wt_rebuild(t, t->d_in_host, stream);
+  if (rc) return rc;
+  const uint32_t Lz = t->L;
+  if (h_bits && Lz && t->W)
+    WT_CUDA(cudaMemcpyAsync(h_bits, t->d_bits, (size_t)Lz * t->W * 4, cudaMemcpyDeviceToHost, st));
+  if (h_rank && Lz)
+    WT_CUDA(cudaMemcpyAsync(h_rank, t->d_rank, (size_t)Lz * (t->NB + 1) * 8, cudaMemcpyDeviceToHost, st));
+  return wt_sync(t);
+}
+
+int wt_info(const wt_tree *t, wt_info_t *info) {
+  if (!t || !info) return WT_ERR_ARG;
+  info->n = t->n;
+  info->sigma = t->sigma;
+  info->symbol_bytes = t->sb;
+  info->levels = t->L;
+  info->reserved = 0;
+  info->words_per_level = t->W;
+  info->blocks = t->NB;
+  info->d_bits = t->d_bits;
+  info->d_rank = reinterpret_cast<uint64_t *>(t->d_rank);
+  info->d_zeros = reinterpret_cast<uint64_t *>(t->d_zeros);
+  info->d_node_start = reinterpret_cast<uint64_t *>(t->d_node_start);
+  return WT_OK;
+}
+
+int wt_profile(wt_tree *t, int enable) {
+  if (!t) return WT_ERR_ARG;
+  if (enable && !t->ev) {
+    t->ev = new (std::nothrow) cudaEvent_t[2 * kMaxProfiled]();
+    t->ev_kind = new (std::nothrow) int32_t[kMaxProfiled]();
+    if (!t->ev || !t->ev_kind) return WT_ERR_OOM;
+    for (uint32_t i = 0; i < 2 * kMaxProfiled; ++i) WT_CUDA(cudaEventCreate(&t->ev[i]));
+  }
+  t->profile = enable != 0;
+  t->n_ev = 0;
+  return WT_OK;
+}
+
+int wt_profile_read(wt_tree *t, float *ms, int32_t *kind, int32_t cap) {
+  if (!t) return WT_ERR_ARG;
+  if (!t->ev) return 0;
+  const int n = t->n_ev;
+  for (int i = 0; i < n && i < cap; ++i) {
+    float v = 0.f;
+    if (cudaEventElapsedTime(&v, t->ev[2 * i], t->ev[2 * i + 1]) != cudaSuccess) {
+      (void)cudaGetLastError();
+      v = -1.f;
+    }
+    if (ms) ms[i] = v;
+    if (kind) kind[i] = t->ev_kind[i];
+  }
+  return n;
+}
+
+int wt_kernels_per_build(const wt_tree *t) {
+  if (!t) return WT_ERR_ARG;
+  if (t->n == 0) return 0;
+  int k = 2 + (tables_blocks(t->L) ? 1 : 0);  // pre-pass, histogram scan, tables
+  if (t->L >= 2) k += (int)(t->L - 1) + 1;    // splits + last level
+  return k;
+}
+
+int wt_free(wt_tree *t) {
+  if (!t) return WT_OK;
+  cudaStreamSynchronize(t->stream);
+  (void)cudaGetLastError();
+  release(t);
+  delete t;
+  return WT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+// Host-side tree object shared by the build and query translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wt.h"
+
+namespace wtk {
+
+constexpr uint32_t kMaxLevels = 26;     // 2^L histogram bins must fit comfortably
+constexpr uint32_t kPasses = 32;        // ticket counters per build (passes <= 3 + L)
+constexpr uint32_t kCtrlWords = 64;     // [0,32) tickets, [32] error, rest reserved
+constexpr uint32_t kCtrlErr = 32;
+constexpr uint32_t kMaxProfiled = 2048;  // kernel launches recorded per profiling window
+
+enum KernelKind : int32_t { kPrepass = 0, kHistScan = 1, kTables = 2, kSplit = 3, kLeaf = 4 };
+
+}  // namespace wtk
+
+struct wt_tree {
+  uint64_t n = 0;
+  uint32_t sigma = 0, sb = 0, L = 0;
+  uint64_t W = 0, NB = 0;
+  uint32_t threads = 0;         // CTA size of the level passes
+  uint64_t T = 0;               // symbols per tile
+  uint64_t NT = 0;              // tiles per level
+  wt_config cfg{};
+  int sms = 0;
+
+  // outputs
+  uint32_t *d_bits = nullptr;
+  unsigned long long *d_rank = nullptr;
+  unsigned long long *d_zeros = nullptr;
+  unsigned long long *d_node_start = nullptr;
+  // scratch
+  uint2 *d_tab = nullptr;       // per level l (heap offset 2^l - 1): {O_l[p], E_{l+1}[2p+1]-O_l[p]}
+  uint32_t *d_ctrl = nullptr;   // kCtrlWords control words followed by the 2^L histogram
+  uint32_t *d_hist = nullptr;
+  void *d_buf[2] = {nullptr, nullptr};
+  size_t buf_bytes = 0;
+  unsigned long long *d_status = nullptr;
+  size_t status_n = 0;
+  void *d_in_host = nullptr;    // device staging of wt_build_host input (lazy)
+
+  uint32_t build_count = 0;
+  cudaStream_t stream = nullptr;
+  int sticky_error = 0;
+
+  bool profile = false;
+  cudaEvent_t *ev = nullptr;      // 2 * kMaxProfiled events, created on first use
+  int32_t *ev_kind = nullptr;
+  int n_ev = 0;                   // launches recorded since wt_profile(tree, 1)
+};

@@ -1,0 +1,330 @@
+"""Python binding of libwt.so (include/wt.h): argument marshalling only.
+
+Every step of the construction and of the queries runs in the CUDA library;
+this module converts torch tensors / numpy arrays to pointers and back.
+PyTorch provides device memory and streams.  There is no CPU fallback: if
+the library is not built, or no GPU is present, calls raise.
+
+The functions named ``wt_*`` mirror the C ABI one to one; ``WaveletTree``
+wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WT_OK = 0
+WT_ERR_ARG = -1
+WT_ERR_OOM = -2
+WT_ERR_CUDA = -3
+WT_ERR_SYMBOL = -4
+WT_ERR_TIMEOUT = -5
+ERROR_NAMES = {WT_ERR_ARG: "WT_ERR_ARG", WT_ERR_OOM: "WT_ERR_OOM", WT_ERR_CUDA: "WT_ERR_CUDA",
+               WT_ERR_SYMBOL: "WT_ERR_SYMBOL", WT_ERR_TIMEOUT: "WT_ERR_TIMEOUT"}
+
+KERNEL_KINDS = {0: "prepass", 1: "hist_scan", 2: "tables", 3: "split", 4: "leaf"}
+
+
+class WTError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        super().__init__(f"{what}: {ERROR_NAMES.get(code, code)}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tile_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("spin_limit", ctypes.c_uint32), ("debug_skip_publish", ctypes.c_uint32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("sigma", ctypes.c_uint32),
+                ("symbol_bytes", ctypes.c_uint32), ("levels", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("words_per_level", ctypes.c_uint64),
+                ("blocks", ctypes.c_uint64), ("d_bits", ctypes.c_void_p),
+                ("d_rank", ctypes.c_void_p), ("d_zeros", ctypes.c_void_p),
+                ("d_node_start", ctypes.c_void_p)]
+
+
+_lib = None
+_cudart = None
+P = ctypes.c_void_p
+U64 = ctypes.c_uint64
+U32 = ctypes.c_uint32
+I32 = ctypes.c_int32
+
+# every entry point declared in include/wt.h, with its ctypes signature
+SIGNATURES = {
+    "wt_create": (ctypes.c_int, [U64, U32, U32, ctypes.POINTER(Config), ctypes.POINTER(P)]),
+    "wt_rebuild": (ctypes.c_int, [P, P, P]),
+    "wt_build": (ctypes.c_int, [P, U64, U32, U32, P, ctypes.POINTER(P)]),
+    "wt_build_ex": (ctypes.c_int, [P, U64, U32, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
+    "wt_build_host": (ctypes.c_int, [P, P, P, P, P]),
+    "wt_sync": (ctypes.c_int, [P]),
+    "wt_info": (ctypes.c_int, [P, ctypes.POINTER(Info)]),
+    "wt_access": (ctypes.c_int, [P, P, U64, P, P]),
+    "wt_rank": (ctypes.c_int, [P, P, P, U64, P, P]),
+    "wt_select": (ctypes.c_int, [P, P, P, U64, P, P]),
+    "wt_profile": (ctypes.c_int, [P, ctypes.c_int]),
+    "wt_profile_read": (ctypes.c_int, [P, P, P, I32]),
+    "wt_free": (ctypes.c_int, [P]),
+    "wt_kernels_per_build": (ctypes.c_int, [P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libwt.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _rt():
+    """The CUDA runtime the library links, for device<->host copies of outputs."""
+    global _cudart
+    if _cudart is None:
+        load()
+        for name in ("libcudart.so.13", "libcudart.so"):
+            try:
+                _cudart = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _cudart is None:
+            raise RuntimeError("libcudart not found")
+        _cudart.cudaMemcpy.restype = ctypes.c_int
+        _cudart.cudaMemcpy.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int]
+    return _cudart
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != WT_OK:
+        raise WTError(rc, what)
+    return rc
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def d2h(dst: np.ndarray, src_ptr: int) -> np.ndarray:
+    if dst.nbytes:
+        rc = _rt().cudaMemcpy(dst.ctypes.data, src_ptr, dst.nbytes, 2)
+        if rc != 0:
+            raise WTError(WT_ERR_CUDA, f"cudaMemcpy D2H ({rc})")
+    return dst
+
+
+# ----------------------------------------------------------------- C ABI mirror
+def wt_create(n: int, sigma: int, symbol_bytes: int, cfg: Config | None = None) -> int:
+    out = P()
+    _check(load().wt_create(n, sigma, symbol_bytes, ctypes.byref(cfg) if cfg else None,
+                            ctypes.byref(out)), "wt_create")
+    return out.value
+
+
+def wt_rebuild(tree: int, d_seq: int, stream=None) -> None:
+    _check(load().wt_rebuild(tree, d_seq, _stream_ptr(stream)), "wt_rebuild")
+
+
+def wt_build(d_seq: int, n: int, sigma: int, symbol_bytes: int, stream=None,
+             cfg: Config | None = None) -> int:
+    out = P()
+    _check(load().wt_build_ex(d_seq, n, sigma, symbol_bytes, ctypes.byref(cfg) if cfg else None,
+                              _stream_ptr(stream), ctypes.byref(out)), "wt_build")
+    return out.value
+
+
+def wt_build_host(tree: int, h_seq: int, h_bits: int | None, h_rank: int | None,
+                  stream=None) -> int:
+    return load().wt_build_host(tree, h_seq, h_bits, h_rank, _stream_ptr(stream))
+
+
+def wt_sync(tree: int) -> int:
+    return load().wt_sync(tree)
+
+
+def wt_info(tree: int) -> Info:
+    info = Info()
+    _check(load().wt_info(tree, ctypes.byref(info)), "wt_info")
+    return info
+
+
+def wt_access(tree: int, d_i: int, m: int, d_out: int, stream=None) -> None:
+    _check(load().wt_access(tree, d_i, m, d_out, _stream_ptr(stream)), "wt_access")
+
+
+def wt_rank(tree: int, d_c: int, d_i: int, m: int, d_out: int, stream=None) -> None:
+    _check(load().wt_rank(tree, d_c, d_i, m, d_out, _stream_ptr(stream)), "wt_rank")
+
+
+def wt_select(tree: int, d_c: int, d_k: int, m: int, d_out: int, stream=None) -> None:
+    _check(load().wt_select(tree, d_c, d_k, m, d_out, _stream_ptr(stream)), "wt_select")
+
+
+def wt_profile(tree: int, enable: bool) -> None:
+    _check(load().wt_profile(tree, 1 if enable else 0), "wt_profile")
+
+
+def wt_profile_read(tree: int, cap: int = 64) -> list[tuple[str, float]]:
+    ms = np.zeros(cap, dtype=np.float32)
+    kind = np.zeros(cap, dtype=np.int32)
+    k = load().wt_profile_read(tree, ms.ctypes.data, kind.ctypes.data, cap)
+    if k < 0:
+        raise WTError(k, "wt_profile_read")
+    return [(KERNEL_KINDS.get(int(kind[i]), str(kind[i])), float(ms[i])) for i in range(min(k, cap))]
+
+
+def wt_kernels_per_build(tree: int) -> int:
+    return int(load().wt_kernels_per_build(tree))
+
+
+def wt_free(tree: int) -> None:
+    load().wt_free(tree)
+
+
+# ----------------------------------------------------------------- convenience
+def _torch_symbols(seq):
+    """Device tensor (uint8 / int16 / int32 views of 1/2/4-byte symbols) from a
+    numpy array or a torch tensor."""
+    import torch
+    if isinstance(seq, np.ndarray):
+        b = seq.dtype.itemsize
+        view = {1: np.uint8, 2: np.int16, 4: np.int32}[b]
+        seq = torch.from_numpy(np.ascontiguousarray(seq).view(view)).cuda()
+    if not seq.is_cuda:
+        seq = seq.cuda()
+    return seq.contiguous()
+
+
+class WaveletTree:
+    """A device-resident levelwise wavelet tree (owns a wt_tree)."""
+
+    def __init__(self, n: int, sigma: int, symbol_bytes: int, tile_threads: int = 0,
+                 ctas_per_sm: int = 0, spin_limit: int = 0, debug_skip_publish: int = 0):
+        self.cfg = Config(tile_threads, ctas_per_sm, spin_limit, debug_skip_publish)
+        self.n, self.sigma, self.symbol_bytes = n, sigma, symbol_bytes
+        self.handle = wt_create(n, sigma, symbol_bytes, self.cfg)
+        self._keep = None
+
+    # construction
+    def build(self, seq, stream=None) -> "WaveletTree":
+        t = _torch_symbols(seq)
+        if t.numel() != self.n or t.element_size() != self.symbol_bytes:
+            raise ValueError("sequence does not match the tree's n / symbol size")
+        self._keep = t  # the input must outlive the enqueued work
+        wt_rebuild(self.handle, t.data_ptr() if self.n else None, stream)
+        return self
+
+    def build_host(self, h_seq: np.ndarray, copy_bits: bool = True, copy_rank: bool = True,
+                   stream=None):
+        inf = self.info()
+        L, W, NB = inf.levels, inf.words_per_level, inf.blocks
+        bits = np.empty((L, W), dtype=np.uint32) if copy_bits else None
+        rank = np.empty((L, NB + 1), dtype=np.uint64) if copy_rank else None
+        h_seq = np.ascontiguousarray(h_seq)
+        rc = wt_build_host(self.handle, h_seq.ctypes.data if self.n else None,
+                           bits.ctypes.data if bits is not None and bits.size else None,
+                           rank.ctypes.data if rank is not None and rank.size else None, stream)
+        return rc, bits, rank
+
+    def sync(self) -> int:
+        return wt_sync(self.handle)
+
+    def check(self) -> None:
+        _check(self.sync(), "build")
+
+    def info(self) -> Info:
+        return wt_info(self.handle)
+
+    def kernels_per_build(self) -> int:
+        return wt_kernels_per_build(self.handle)
+
+    def to_host(self) -> dict:
+        """Synchronise and copy every output to host numpy arrays."""
+        rc = self.sync()
+        inf = self.info()
+        L, W, NB = inf.levels, inf.words_per_level, inf.blocks
+        out = {"status": rc, "L": L, "W": W, "NB": NB}
+        out["bits"] = d2h(np.empty((L, W), dtype=np.uint32), inf.d_bits)
+        out["rank"] = d2h(np.empty((L, NB + 1), dtype=np.uint64), inf.d_rank)
+        out["zeros"] = d2h(np.empty(L, dtype=np.uint64), inf.d_zeros)
+        out["node_start"] = d2h(np.empty((1 << L) + 1, dtype=np.uint64), inf.d_node_start)
+        return out
+
+    # queries
+    def access(self, idx, stream=None):
+        import torch
+        i = torch.as_tensor(np.ascontiguousarray(idx, dtype=np.uint64).view(np.int64)).cuda()
+        out = torch.empty(i.numel(), dtype=torch.int32, device="cuda")
+        wt_access(self.handle, i.data_ptr(), i.numel(), out.data_ptr(), stream)
+        return out
+
+    def rank(self, c, idx, stream=None):
+        import torch
+        cc = torch.as_tensor(np.ascontiguousarray(c, dtype=np.uint32).view(np.int32)).cuda()
+        i = torch.as_tensor(np.ascontiguousarray(idx, dtype=np.uint64).view(np.int64)).cuda()
+        out = torch.empty(i.numel(), dtype=torch.int64, device="cuda")
+        wt_rank(self.handle, cc.data_ptr(), i.data_ptr(), i.numel(), out.data_ptr(), stream)
+        return out
+
+    def select(self, c, k, stream=None):
+        import torch
+        cc = torch.as_tensor(np.ascontiguousarray(c, dtype=np.uint32).view(np.int32)).cuda()
+        kk = torch.as_tensor(np.ascontiguousarray(k, dtype=np.uint64).view(np.int64)).cuda()
+        out = torch.empty(kk.numel(), dtype=torch.int64, device="cuda")
+        wt_select(self.handle, cc.data_ptr(), kk.data_ptr(), kk.numel(), out.data_ptr(), stream)
+        return out
+
+    # measurement
+    def profile(self, enable: bool = True) -> None:
+        wt_profile(self.handle, enable)
+
+    def profile_read(self) -> list[tuple[str, float]]:
+        return wt_profile_read(self.handle)
+
+    def free(self) -> None:
+        if getattr(self, "handle", None):
+            wt_free(self.handle)
+            self.handle = None
+            self._keep = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_tree(seq, sigma: int, **cfg) -> WaveletTree:
+    """Create a tree for `seq` (numpy array or CUDA tensor) and enqueue its build."""
+    if isinstance(seq, np.ndarray):
+        n, b = seq.size, seq.dtype.itemsize
+    else:
+        n, b = seq.numel(), seq.element_size()
+    return WaveletTree(n, sigma, b, **cfg).build(seq)
