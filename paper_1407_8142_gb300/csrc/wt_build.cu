@@ -38,20 +38,7 @@ constexpr uint32_t kScanItems = 8;
 constexpr uint32_t kScanChunk = kScanThreads * kScanItems;
 constexpr uint32_t kDefaultSpin = 1u << 22;
 
-// ------------------------------------------------------------------ bits pass
-struct BitsArgs {
-  const uint8_t *in;  // this level's symbols T_l (16-byte aligned)
-  uint32_t n, L, level, NT, NB;
-  uint64_t W;
-  uint32_t *bits;              // level's bitmap
-  unsigned long long *rank;    // level's directory, NB+1 entries
-  unsigned long long *zeros;   // &zeros[level]
-  uint32_t *ticket;
-  Lookback lb;
-  uint32_t *hist;  // pre-pass only
-  uint32_t sigma;  // pre-pass only
-};
-
+// ------------------------------------------------------------------ helpers
 template <int SB>
 __device__ __forceinline__ void load32(const uint8_t *g, uint32_t my0, uint32_t nv, uint32_t *u) {
   if (my0 + 32 <= nv) {
@@ -85,21 +72,62 @@ __device__ __forceinline__ uint32_t valid_mask(uint32_t my0, uint32_t nv) {
   return (1u << (nv - my0)) - 1u;
 }
 
-// Pre-pass (PREPASS = true: level 0 of S plus histogram and range check) and
-// the last level (PREPASS = false).  Persistent CTAs take tiles in ticket
-// order, so a tile only ever waits on tiles already held by running CTAs.
-template <int SB, int THREADS, bool PREPASS, bool HIST_SMEM>
-__global__ void __launch_bounds__(THREADS) k_bits(BitsArgs a) {
+template <int SB>
+struct SymT;
+template <>
+struct SymT<1> { using type = uint8_t; };
+template <>
+struct SymT<2> { using type = uint16_t; };
+template <>
+struct SymT<4> { using type = uint32_t; };
+
+// Outputs of one level: its bitmap row, directory row and zero count.
+struct LevelOut {
+  uint32_t *bits;
+  unsigned long long *rank;
+  unsigned long long *zeros;
+};
+
+// Write the level's bitmap word, the directory entries that fall in this
+// thread's 32 positions, and (last tile) the level totals.  R = ones before
+// the tile, excl = ones before this thread within the tile.
+template <int THREADS>
+__device__ __forceinline__ void write_level(const LevelOut &o, uint32_t tile, uint32_t NT,
+                                            uint64_t start, uint32_t my0, uint32_t n, uint32_t NB,
+                                            uint64_t W, uint32_t word, uint32_t R, uint32_t excl,
+                                            uint32_t total) {
+  const uint64_t widx = (uint64_t)tile * THREADS + threadIdx.x;
+  if (widx < W) o.bits[widx] = word;
+  if ((threadIdx.x & 15) == 0 && start + my0 < n) o.rank[(start + my0) >> 9] = R + excl;
+  if (tile == NT - 1 && threadIdx.x == 0) {
+    o.rank[NB] = R + total;
+    *o.zeros = (unsigned long long)(n - (R + total));
+  }
+}
+
+// ------------------------------------------------------------------ pre-pass
+struct PrepassArgs {
+  const uint8_t *in;  // S, 16-byte aligned
+  uint32_t n, L, NT, sigma;
+  uint32_t *hist;     // 2^L bins
+  TileCounts cnt;     // level-0 ones per tile
+  uint32_t *ticket;
+  int *err;
+};
+
+// Reads S once: the 2^L-bin histogram (node sizes of every level), the range
+// check, and the level-0 ones of every tile.  Persistent CTAs, tiles by ticket.
+template <int SB, int THREADS, bool HIST_SMEM>
+__global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
   constexpr uint32_t T = 32 * THREADS;
   extern __shared__ __align__(16) uint32_t s_hist[];
   __shared__ uint32_t s_warp[33];
-  __shared__ uint32_t s_tile, s_R;
+  __shared__ uint32_t s_tile;
   const uint32_t tid = threadIdx.x, lane = tid & 31;
-  const uint32_t k = a.L ? a.L - 1 - a.level : 0u;  // L = 0: no bits, check + histogram only
   const uint32_t lmask = (1u << a.L) - 1u;
   const uint32_t nbins = 1u << a.L;
   uint32_t bad = 0;
-  if (PREPASS && HIST_SMEM)
+  if (HIST_SMEM)
     for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
 
   for (;;) {
@@ -112,48 +140,76 @@ __global__ void __launch_bounds__(THREADS) k_bits(BitsArgs a) {
     const uint32_t my0 = 32 * tid;
     uint32_t u[8 * SB];
     load32<SB>(a.in + (start + my0) * SB, my0, nv, u);
-    const uint32_t word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
-    if (PREPASS) {
+    const uint32_t word = a.L ? pack_bits<SB>(u, a.L - 1) & valid_mask(my0, nv) : 0u;
 #pragma unroll 4
-      for (int q = 0; q < 32; ++q) {
-        const bool valid = my0 + q < nv;
-        const uint32_t s = symbol_at<SB>(u, q);
-        if (valid) bad |= (uint32_t)(s >= a.sigma);
-        if (HIST_SMEM) {
-          if (valid) atomicAdd(&s_hist[s & lmask], 1u);
-        } else {
-          const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
-          if (valid) {
-            const uint32_t v = s & lmask;
-            const uint32_t peers = __match_any_sync(am, v);
-            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
-          }
+    for (int q = 0; q < 32; ++q) {
+      const bool valid = my0 + q < nv;
+      const uint32_t s = symbol_at<SB>(u, q);
+      if (valid) bad |= (uint32_t)(s >= a.sigma);
+      if (HIST_SMEM) {
+        if (valid) atomicAdd(&s_hist[s & lmask], 1u);
+      } else {
+        const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
+        if (valid) {
+          const uint32_t v = s & lmask;
+          const uint32_t peers = __match_any_sync(am, v);
+          if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
         }
       }
     }
     uint32_t total;
-    const uint32_t excl = block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
-    if (tid < 32) {
-      const uint32_t R = lookback(a.lb, tile, 0, total);
-      if (tid == 0) s_R = R;
-    }
-    __syncthreads();
-    const uint32_t R = s_R;
-    const uint64_t widx = (uint64_t)tile * THREADS + tid;
-    if (widx < a.W) a.bits[widx] = word;
-    if ((tid & 15) == 0 && start + my0 < a.n) a.rank[(start + my0) >> 9] = R + excl;
-    if (tile == a.NT - 1 && tid == 0) {
-      a.rank[a.NB] = R + total;
-      *a.zeros = (unsigned long long)(a.n - (R + total));
+    block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
+    if (tid == 0 && a.L) {
+      a.cnt.c0[tile] = total;
+      if (total) {
+        atomicAdd(&a.cnt.c1[tile >> 6], total);
+        atomicAdd(&a.cnt.c2[tile >> 12], total);
+      }
     }
   }
-  if (PREPASS) {
-    if (bad) latch_error(a.lb.err, WT_ERR_SYMBOL);
-    if (HIST_SMEM) {
-      __syncthreads();
-      for (uint32_t i = tid; i < nbins; i += THREADS)
-        if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
-    }
+  if (bad) latch_error(a.err, WT_ERR_SYMBOL);
+  if (HIST_SMEM) {
+    __syncthreads();
+    for (uint32_t i = tid; i < nbins; i += THREADS)
+      if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+  }
+}
+
+// ------------------------------------------------------------------ last level
+struct LeafArgs {
+  const uint8_t *in;  // T_{L-1}, 16-byte aligned
+  uint32_t n, L, NT, NB;
+  uint64_t W;
+  LevelOut out;
+  TileCounts cnt;     // ones of this level per tile
+  uint32_t *ticket;
+};
+
+// Level L-1 (and level 0 when L = 1): bits and directory; its nodes have
+// range 2 and no children.
+template <int SB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_leaf(LeafArgs a) {
+  constexpr uint32_t T = 32 * THREADS;
+  __shared__ unsigned long long s_warp[33];
+  __shared__ uint32_t s_tile;
+  const uint32_t tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= a.NT) break;
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    const uint32_t my0 = 32 * tid;
+    const uint32_t share = prefix_share<THREADS>(a.cnt, tile);
+    uint32_t u[8 * SB];
+    load32<SB>(a.in + (start + my0) * SB, my0, nv, u);
+    const uint32_t word = pack_bits<SB>(u, 0) & valid_mask(my0, nv);
+    unsigned long long tot;
+    const unsigned long long ex =
+        block_exclusive_scan64<THREADS>(((unsigned long long)share << 32) | __popc(word), s_warp, &tot);
+    write_level<THREADS>(a.out, tile, a.NT, start, my0, a.n, a.NB, a.W, word,
+                         (uint32_t)(tot >> 32), (uint32_t)ex, (uint32_t)tot);
   }
 }
 
@@ -162,61 +218,77 @@ struct SplitArgs {
   const uint8_t *in;   // T_l, 16-byte aligned
   uint8_t *out;        // T_{l+1}
   int in_padded;       // in holds whole tiles (scratch buffer) -> copy full tiles
-  uint32_t n, L, level, NT, NB;
+  uint32_t n, L, level, NT, NB, log2T;
   uint64_t W;
   const uint2 *tab;    // this level's {O_l[p], E_{l+1}[2p+1] - O_l[p]}
-  uint32_t *bits;      // level's bitmap, or nullptr when already written
-  unsigned long long *rank;
-  unsigned long long *zeros;
-  const unsigned long long *rank_known;  // level's directory when already built (level 0)
+  LevelOut lo;
+  TileCounts cin;      // ones of level l per tile of T_l
+  TileCounts cout;     // ones of level l+1 per tile of T_{l+1} (accumulated here)
   uint32_t *ticket;
-  Lookback lb;
+  uint32_t spin_limit;
+  int *err;
 };
 
-// Copy `len` bytes from shared memory (byte offset soff of a 16-byte aligned
-// array) to global gout[goff..): unaligned head and tail bytes singly, the
-// body as aligned 16-byte stores.  Writes past gbound are dropped (only
-// reachable after a device error).
-template <int THREADS>
+// Bit k1 of the symbols packed in a 32-bit word, counted.
+template <int SB>
+__device__ __forceinline__ uint32_t count_bit(uint32_t w, uint32_t k1) {
+  if (SB == 1) return __popc((w >> k1) & 0x01010101u);
+  if (SB == 2) return __popc((w >> k1) & 0x00010001u);
+  return (w >> k1) & 1u;
+}
+
+// Copy one run of `len` symbols from shared memory (byte offset soff of a
+// 16-byte aligned array) to global symbol position gpos: unaligned head and
+// tail bytes singly, the body as aligned 16-byte stores.  While copying,
+// count bit k1 of the copied symbols into cnt_a (destination tile of the
+// run's first symbol) and cnt_b (the next tile).  Writes past n are dropped
+// (reachable only after a device error).
+template <int SB, int THREADS>
 __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, uint8_t *gout,
-                                         uint64_t goff, uint32_t len, uint64_t gbound) {
-  if (goff >= gbound) return;
-  if (goff + len > gbound) len = (uint32_t)(gbound - goff);
+                                         uint64_t gpos, uint32_t len, uint32_t n, uint32_t log2T,
+                                         uint32_t k1, uint32_t &cnt_a, uint32_t &cnt_b) {
+  if (gpos >= n) return;
+  if (gpos + len > n) len = (uint32_t)(n - gpos);
   if (len == 0) return;
-  uint8_t *dst = gout + goff;
+  const uint64_t split_at = ((gpos >> log2T) + 1) << log2T;  // first position of the next tile
+  uint8_t *dst = gout + gpos * SB;
+  const uint32_t bytes = len * SB;
   const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbase);
   const uint32_t mis = (uint32_t)(reinterpret_cast<uintptr_t>(dst) & 15u);
-  const uint32_t head = min(len, (16u - mis) & 15u);
-  const uint32_t nch = (len - head) >> 4;
+  const uint32_t head = min(bytes, (16u - mis) & 15u);
+  const uint32_t nch = (bytes - head) >> 4;
   const uint32_t tail0 = head + (nch << 4);
-  const uint32_t tail = len - tail0;
+  const uint32_t tail = bytes - tail0;
   const uint32_t t = threadIdx.x;
-  if (t < head) {
-    dst[t] = sb[soff + t];
-  } else if (t < head + tail) {
-    const uint32_t o = tail0 + (t - head);
+  if (t < head + tail) {
+    const uint32_t o = t < head ? t : tail0 + (t - head);
     dst[o] = sb[soff + o];
+    if (o % SB == 0) {  // first byte of a symbol: count it
+      uint32_t s;
+      if (SB == 1) s = sb[soff + o];
+      else if (SB == 2) s = *reinterpret_cast<const uint16_t *>(sb + soff + o);
+      else s = *reinterpret_cast<const uint32_t *>(sb + soff + o);
+      const uint32_t one = (s >> k1) & 1u;
+      if (gpos + o / SB >= split_at) cnt_b += one;
+      else cnt_a += one;
+    }
   }
   for (uint32_t c = t; c < nch; c += THREADS) {
     const uint32_t o = head + (c << 4);
-    *reinterpret_cast<uint4 *>(dst + o) = lds16_unaligned(sbase, soff + o);
+    const uint4 v = lds16_unaligned(sbase, soff + o);
+    *reinterpret_cast<uint4 *>(dst + o) = v;
+    const uint32_t ones = count_bit<SB>(v.x, k1) + count_bit<SB>(v.y, k1) +
+                          count_bit<SB>(v.z, k1) + count_bit<SB>(v.w, k1);
+    if (gpos + o / SB >= split_at) cnt_b += ones;
+    else cnt_a += ones;
   }
 }
-
-template <int SB>
-struct SymT;
-template <>
-struct SymT<1> { using type = uint8_t; };
-template <>
-struct SymT<2> { using type = uint16_t; };
-template <>
-struct SymT<4> { using type = uint32_t; };
 
 template <int SB, int THREADS>
 constexpr uint32_t split_smem_bytes() {
   // two input tiles, one output tile (+16 bytes of slack for unaligned reads),
-  // per-thread bit words and ones-prefixes, two mbarriers
-  return 3u * 32u * THREADS * SB + 16u + 8u * THREADS + 16u;
+  // per-thread bit words and ones-prefixes, two mbarriers, run counters
+  return 3u * 32u * THREADS * SB + 16u + 8u * THREADS + 16u + 16u;
 }
 
 template <int SB, int THREADS>
@@ -231,15 +303,15 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
   uint32_t *const sWord = reinterpret_cast<uint32_t *>(smem + 3 * TB + 16);
   uint32_t *const sPref = sWord + THREADS;
   uint64_t *const bar = reinterpret_cast<uint64_t *>(sPref + THREADS);
-  __shared__ uint32_t s_warp[33];
+  uint32_t *const sCnt = reinterpret_cast<uint32_t *>(bar + 2);  // 4 run counters
+  __shared__ unsigned long long s_warp[33];
   __shared__ uint32_t s_ticket[2];
-  __shared__ uint32_t s_R;
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t k = a.L - 1 - a.level;
-  const uint32_t pshift = a.L - a.level;
+  const uint32_t k = a.L - 1 - a.level;   // bit of this level
+  const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
+  const uint32_t pshift = a.L - a.level;  // node prefix = symbol >> pshift
   const uint32_t lmask = (1u << a.L) - 1u;
-  const uint32_t spin = a.lb.spin_limit;
 
   auto issue = [&](uint32_t tile, int buf) {
     const uint64_t start = (uint64_t)tile * T;
@@ -257,6 +329,7 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     s_ticket[0] = t0;
     if (t0 < a.NT) issue(t0, 0);
   }
+  if (tid < 4) sCnt[tid] = 0;
   __syncthreads();
 
   for (uint32_t it = 0;; ++it) {
@@ -272,13 +345,15 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
         issue(nx, buf ^ 1);
       }
     }
-    const bool ok = mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, spin, a.lb.err);
+    // the tile's exclusive prefix: loads issued before waiting for the data
+    const uint32_t share = prefix_share<THREADS>(a.cin, tile);
+    const bool ok = mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, a.spin_limit, a.err);
     if (__syncthreads_or(!ok)) {
       // The copy did not land in time: wait once more (bounded) for the
       // copies this CTA started, then stop.
       if (tid == 0) {
-        mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, spin, a.lb.err);
-        mbar_wait_bounded(&bar[buf ^ 1], ((it + 1) >> 1) & 1u, spin, a.lb.err);
+        mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, a.spin_limit, a.err);
+        mbar_wait_bounded(&bar[buf ^ 1], ((it + 1) >> 1) & 1u, a.spin_limit, a.err);
       }
       __syncthreads();
       return;
@@ -306,28 +381,14 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
       }
     }
     const uint32_t word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
-    uint32_t total;
-    const uint32_t excl = block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
+    unsigned long long tot;
+    const uint32_t excl = (uint32_t)block_exclusive_scan64<THREADS>(
+        ((unsigned long long)share << 32) | __popc(word), s_warp, &tot);
+    const uint32_t total = (uint32_t)tot, R = (uint32_t)(tot >> 32);
     sWord[tid] = word;
     sPref[tid] = excl;
-    if (a.rank_known) {
-      // level 0: the pre-pass already holds R(tile start) in its directory
-      if (tid == 0) s_R = (uint32_t)a.rank_known[start >> 9];
-    } else if (warp == 0) {
-      const uint32_t R = lookback(a.lb, tile, 0, total);
-      if (lane == 0) s_R = R;
-    }
+    write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, excl, total);
     __syncthreads();
-    const uint32_t R = s_R;
-    if (a.bits) {
-      const uint64_t widx = (uint64_t)tile * THREADS + tid;
-      if (widx < a.W) a.bits[widx] = word;
-      if ((tid & 15) == 0 && start + my0 < a.n) a.rank[(start + my0) >> 9] = R + excl;
-      if (tile == a.NT - 1 && tid == 0) {
-        a.rank[a.NB] = R + total;
-        *a.zeros = (unsigned long long)(a.n - (R + total));
-      }
-    }
 
     // Pass B: stable split of the tile into shared memory, zeros first.
     // Warp w owns tile positions [1024w, 1024w + 1024); step q covers the
@@ -363,25 +424,57 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     }
     __syncthreads();
 
-    // Phase 2: write the tile's runs to T_{l+1}.
+    // Phase 2: write the tile's runs to T_{l+1}, counting the next level's
+    // ones per destination tile.
     const uint32_t Zb = (uint32_t)start - R;  // zeros of level l before the tile
     const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
     const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
-    const uint64_t gbound = (uint64_t)a.n * SB;
     if (pf == pl) {
       // the whole tile lies in one node: one run of zeros, one run of ones
       const uint2 tb = __ldg(&a.tab[pf]);
       const uint32_t *sO = reinterpret_cast<const uint32_t *>(sOut);
-      copy_run<THREADS>(sO, 0, a.out, (uint64_t)(tb.x + Zb) * SB, Zt * SB, gbound);
-      copy_run<THREADS>(sO, Zt * SB, a.out, (uint64_t)(tb.y + R) * SB, (nv - Zt) * SB, gbound);
+      uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
+      const uint64_t g0 = (uint64_t)tb.x + Zb, g1 = (uint64_t)tb.y + R;
+      copy_run<SB, THREADS>(sO, 0, a.out, g0, Zt, a.n, a.log2T, k1, c0a, c0b);
+      copy_run<SB, THREADS>(sO, Zt * SB, a.out, g1, nv - Zt, a.n, a.log2T, k1, c1a, c1b);
+      const uint32_t v0 = __reduce_add_sync(0xFFFFFFFFu, c0a);
+      const uint32_t v1 = __reduce_add_sync(0xFFFFFFFFu, c0b);
+      const uint32_t v2 = __reduce_add_sync(0xFFFFFFFFu, c1a);
+      const uint32_t v3 = __reduce_add_sync(0xFFFFFFFFu, c1b);
+      if (lane == 0) {
+        if (v0) atomicAdd(&sCnt[0], v0);
+        if (v1) atomicAdd(&sCnt[1], v1);
+        if (v2) atomicAdd(&sCnt[2], v2);
+        if (v3) atomicAdd(&sCnt[3], v3);
+      }
+      __syncthreads();
+      if (tid < 4) {
+        const uint32_t v = sCnt[tid];
+        sCnt[tid] = 0;
+        const uint64_t g = tid < 2 ? g0 : g1;
+        const uint64_t dt = (g >> a.log2T) + (tid & 1);
+        if (v && dt < a.NT) counts_add(a.cout, (uint32_t)dt, v);
+      }
     } else {
       Sym *outS = reinterpret_cast<Sym *>(a.out);
-      for (uint32_t kk = tid; kk < nv; kk += THREADS) {
-        const Sym s = sOutS[kk];
-        const uint32_t p = ((uint32_t)s & lmask) >> pshift;
-        const uint2 tb = __ldg(&a.tab[p]);
-        const uint32_t dest = kk < Zt ? tb.x + Zb + kk : tb.y + R + (kk - Zt);
-        if (dest < a.n) outS[dest] = s;
+      for (uint32_t base = 0; base < nv; base += THREADS) {
+        const uint32_t kk = base + tid;
+        const bool valid = kk < nv;
+        uint32_t dest = 0xFFFFFFFFu, bit = 0;
+        if (valid) {
+          const Sym s = sOutS[kk];
+          const uint32_t p = ((uint32_t)s & lmask) >> pshift;
+          const uint2 tb = __ldg(&a.tab[p]);
+          dest = kk < Zt ? tb.x + Zb + kk : tb.y + R + (kk - Zt);
+          if (dest < a.n) outS[dest] = s;
+          else dest = 0xFFFFFFFFu;
+          bit = ((uint32_t)s >> k1) & 1u;
+        }
+        const uint32_t dt = dest >> a.log2T;
+        const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit && dest != 0xFFFFFFFFu);
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dt);
+        const uint32_t c = __popc(ones & peers);
+        if (dest != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1) && c) counts_add(a.cout, dt, c);
       }
     }
     __syncthreads();
@@ -537,12 +630,23 @@ struct Launcher {
     Lookback l;
     l.status = t->d_status;
     l.epoch = epoch_base + pass;
-    l.spin_limit = t->cfg.spin_limit ? t->cfg.spin_limit : kDefaultSpin;
+    l.spin_limit = spin();
     l.skip = t->cfg.debug_skip_publish;
-    l.err = reinterpret_cast<int *>(t->d_ctrl + kCtrlErr);
+    l.err = err();
     return l;
   }
+  uint32_t spin() const { return t->cfg.spin_limit ? t->cfg.spin_limit : kDefaultSpin; }
+  int *err() const { return reinterpret_cast<int *>(t->d_ctrl + kCtrlErr); }
   uint32_t *ticket() const { return t->d_ctrl + pass; }
+  TileCounts counts(uint32_t level) const {
+    const uint64_t NT = t->NT;
+    uint32_t *base = t->d_counts + (uint64_t)level * t->counts_per_level;
+    return TileCounts{base, base + NT, base + NT + (NT >> 6) + 1};
+  }
+  LevelOut out(uint32_t level) const {
+    return LevelOut{t->d_bits + (uint64_t)level * t->W, t->d_rank + (uint64_t)level * (t->NB + 1),
+                    t->d_zeros + level};
+  }
 
   void before(int kind) {
     if (t->profile && t->n_ev < (int)kMaxProfiled) {
@@ -559,39 +663,53 @@ struct Launcher {
 };
 
 template <int SB, int THREADS>
-int launch_bits(Launcher &ln, const uint8_t *in, uint32_t level, bool prepass) {
+int launch_prepass(Launcher &ln, const uint8_t *in) {
   wt_tree *t = ln.t;
-  BitsArgs a;
+  PrepassArgs a;
   a.in = in;
   a.n = (uint32_t)t->n;
   a.L = t->L;
-  a.level = level;
   a.NT = (uint32_t)t->NT;
-  a.NB = (uint32_t)t->NB;
-  a.W = t->W;
-  a.bits = t->d_bits + (uint64_t)level * t->W;
-  a.rank = t->d_rank + (uint64_t)level * (t->NB + 1);
-  a.zeros = t->d_zeros + level;
-  a.ticket = ln.ticket();
-  a.lb = ln.lb();
-  a.hist = t->d_hist;
   a.sigma = t->sigma;
+  a.hist = t->d_hist;
+  a.cnt = ln.counts(0);
+  a.ticket = ln.ticket();
+  a.err = ln.err();
   const uint32_t nbins = 1u << t->L;
-  ln.before(prepass ? kPrepass : kLeaf);
-  if (prepass && nbins <= kHistSmemMaxBins) {
-    auto kern = k_bits<SB, THREADS, true, true>;
+  ln.before(kPrepass);
+  if (nbins <= kHistSmemMaxBins) {
+    auto kern = k_prepass<SB, THREADS, true>;
     const size_t sm = nbins * sizeof(uint32_t);
     const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
     kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
-  } else if (prepass) {
-    auto kern = k_bits<SB, THREADS, true, false>;
-    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, 0, t->sms, t->cfg.ctas_per_sm));
-    kern<<<std::max(grid, 1), THREADS, 0, ln.st>>>(a);
   } else {
-    auto kern = k_bits<SB, THREADS, false, false>;
+    auto kern = k_prepass<SB, THREADS, false>;
     const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, 0, t->sms, t->cfg.ctas_per_sm));
     kern<<<std::max(grid, 1), THREADS, 0, ln.st>>>(a);
   }
+  ln.after();
+  ++ln.pass;
+  WT_CUDA(cudaGetLastError());
+  return WT_OK;
+}
+
+template <int SB, int THREADS>
+int launch_leaf(Launcher &ln, const uint8_t *in, uint32_t level) {
+  wt_tree *t = ln.t;
+  LeafArgs a;
+  a.in = in;
+  a.n = (uint32_t)t->n;
+  a.L = t->L;
+  a.NT = (uint32_t)t->NT;
+  a.NB = (uint32_t)t->NB;
+  a.W = t->W;
+  a.out = ln.out(level);
+  a.cnt = ln.counts(level);
+  a.ticket = ln.ticket();
+  auto kern = k_leaf<SB, THREADS>;
+  const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, 0, t->sms, t->cfg.ctas_per_sm));
+  ln.before(kLeaf);
+  kern<<<std::max(grid, 1), THREADS, 0, ln.st>>>(a);
   ln.after();
   ++ln.pass;
   WT_CUDA(cudaGetLastError());
@@ -610,14 +728,15 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.level = level;
   a.NT = (uint32_t)t->NT;
   a.NB = (uint32_t)t->NB;
+  a.log2T = 5 + (uint32_t)__builtin_ctz(THREADS);
   a.W = t->W;
   a.tab = t->d_tab + ((1u << level) - 1);
-  a.bits = level ? t->d_bits + (uint64_t)level * t->W : nullptr;
-  a.rank = t->d_rank + (uint64_t)level * (t->NB + 1);
-  a.zeros = t->d_zeros + level;
-  a.rank_known = level ? nullptr : t->d_rank;
+  a.lo = ln.out(level);
+  a.cin = ln.counts(level);
+  a.cout = ln.counts(level + 1);
   a.ticket = ln.ticket();
-  a.lb = ln.lb();
+  a.spin_limit = ln.spin();
+  a.err = ln.err();
   auto kern = k_split<SB, THREADS>;
   constexpr uint32_t sm = split_smem_bytes<SB, THREADS>();
   static bool attr_set = false;
@@ -672,9 +791,9 @@ template <int SB, int THREADS>
 int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
   Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
   int rc;
-  if ((rc = launch_bits<SB, THREADS>(ln, seq, 0, true))) return rc;
+  if ((rc = launch_prepass<SB, THREADS>(ln, seq))) return rc;
   if ((rc = launch_tables(ln))) return rc;
-  if (t->L < 2) return WT_OK;
+  if (t->L == 0) return WT_OK;
   const uint8_t *in = seq;
   bool padded = seq_padded;
   for (uint32_t l = 0; l + 1 < t->L; ++l) {
@@ -683,7 +802,7 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
     in = out;
     padded = true;
   }
-  return launch_bits<SB, THREADS>(ln, in, t->L - 1, false);
+  return launch_leaf<SB, THREADS>(ln, in, t->L - 1);
 }
 
 template <int SB>
@@ -777,8 +896,11 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
   if ((e = cudaMalloc(&t->d_zeros, Lz * 8))) return fail(e);
   if ((e = cudaMalloc(&t->d_node_start, (nbins + 1) * 8))) return fail(e);
   if ((e = cudaMalloc(&t->d_tab, std::max<uint64_t>(1, nbins / 2) * sizeof(uint2)))) return fail(e);
-  if ((e = cudaMalloc(&t->d_ctrl, (kCtrlWords + nbins) * 4))) return fail(e);
+  t->counts_per_level = t->NT + (t->NT >> 6) + 1 + (t->NT >> 12) + 1;
+  t->ctrl_words = kCtrlWords + nbins + (uint64_t)Lz * t->counts_per_level;
+  if ((e = cudaMalloc(&t->d_ctrl, t->ctrl_words * 4))) return fail(e);
   t->d_hist = t->d_ctrl + kCtrlWords;
+  t->d_counts = t->d_hist + nbins;
   t->buf_bytes = t->NT * t->T * symbol_bytes + 16;
   if (L >= 2) {
     if ((e = cudaMalloc(&t->d_buf[0], t->buf_bytes))) return fail(e);
@@ -800,7 +922,7 @@ int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
   t->sticky_error = 0;
   ++t->build_count;
   const uint64_t nbins = 1ull << t->L;
-  WT_CUDA(cudaMemsetAsync(t->d_ctrl, 0, (kCtrlWords + nbins) * 4, st));
+  WT_CUDA(cudaMemsetAsync(t->d_ctrl, 0, t->ctrl_words * 4, st));
   const uint8_t *seq = static_cast<const uint8_t *>(d_seq);
   bool padded = false;
   if (t->n && (reinterpret_cast<uintptr_t>(seq) & 15u)) {
@@ -918,7 +1040,7 @@ int wt_kernels_per_build(const wt_tree *t) {
   if (!t) return WT_ERR_ARG;
   if (t->n == 0) return 0;
   int k = 2 + (tables_blocks(t->L) ? 1 : 0);  // pre-pass, histogram scan, tables
-  if (t->L >= 2) k += (int)(t->L - 1) + 1;    // splits + last level
+  if (t->L >= 1) k += (int)(t->L - 1) + 1;    // splits + last level
   return k;
 }
 

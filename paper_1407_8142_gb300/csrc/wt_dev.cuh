@@ -150,6 +150,78 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
   return (warp ? s_warp[warp - 1] : 0u) + x - v;
 }
 
+// 64-bit variant: the low 32 bits carry per-thread counts whose exclusive
+// prefix is wanted, the high 32 bits carry terms whose block total is wanted
+// (no carry crosses from the low half: block sums stay below 2^32).
+template <int THREADS>
+__device__ __forceinline__ unsigned long long block_exclusive_scan64(unsigned long long v,
+                                                                     unsigned long long *s_warp,
+                                                                     unsigned long long *total) {
+  constexpr int NW = THREADS / 32;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < (uint32_t)NW ? s_warp[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  *total = s_warp[NW - 1];
+  return (warp ? s_warp[warp - 1] : 0ull) + x - v;
+}
+
+// ------------------------------------------------------------ tile counts
+// Ones of one level per tile of T symbols, kept at three granularities (per
+// tile, per 64 tiles, per 4096 tiles) so that the exclusive prefix of any
+// tile t is a sum of (t >> 12) + ((t >> 6) & 63) + (t & 63) terms, loaded in
+// parallel by the tile's threads.  The pass over level l adds the counts of
+// level l+1 for the tiles of T_{l+1} its output lands in; the pass over level
+// l+1 then needs no inter-tile wait at all.
+struct TileCounts {
+  uint32_t *c0, *c1, *c2;
+};
+
+__device__ __forceinline__ void counts_add(const TileCounts &c, uint32_t tile, uint32_t v) {
+  if (v == 0) return;
+  atomicAdd(&c.c0[tile], v);
+  atomicAdd(&c.c1[tile >> 6], v);
+  atomicAdd(&c.c2[tile >> 12], v);
+}
+
+__device__ __forceinline__ uint32_t prefix_terms(uint32_t t) {
+  return (t >> 12) + ((t >> 6) & 63u) + (t & 63u);
+}
+
+__device__ __forceinline__ const uint32_t *prefix_term(const TileCounts &c, uint32_t t, uint32_t j) {
+  const uint32_t n2 = t >> 12;
+  if (j < n2) return c.c2 + j;
+  j -= n2;
+  const uint32_t n1 = (t >> 6) & 63u;
+  if (j < n1) return c.c1 + ((t >> 12) << 6) + j;
+  j -= n1;
+  return c.c0 + ((t >> 6) << 6) + j;
+}
+
+// This thread's share of the exclusive prefix of tile t (sum over threads).
+template <int THREADS>
+__device__ __forceinline__ uint32_t prefix_share(const TileCounts &c, uint32_t t) {
+  const uint32_t nt = prefix_terms(t);
+  uint32_t s = 0;
+  for (uint32_t j = threadIdx.x; j < nt; j += THREADS) s += __ldcg(prefix_term(c, t, j));
+  return s;
+}
+
 // ------------------------------------------------------------ bit packing
 // A thread holds 32 consecutive symbols as 8*SB little-endian 32-bit words.
 // Pack bit k of each symbol into one 32-bit word, symbol q -> bit q.

@@ -36,6 +36,9 @@ struct wt_tree {
   uint2 *d_tab = nullptr;       // per level l (heap offset 2^l - 1): {O_l[p], E_{l+1}[2p+1]-O_l[p]}
   uint32_t *d_ctrl = nullptr;   // kCtrlWords control words followed by the 2^L histogram
   uint32_t *d_hist = nullptr;
+  uint32_t *d_counts = nullptr;   // per level: ones per tile, per 64 tiles, per 4096 tiles
+  uint64_t counts_per_level = 0;
+  uint64_t ctrl_words = 0;        // control words + histogram + tile counts (cleared per build)
   void *d_buf[2] = {nullptr, nullptr};
   size_t buf_bytes = 0;
   unsigned long long *d_status = nullptr;

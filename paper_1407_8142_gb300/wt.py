@@ -185,7 +185,7 @@ def wt_profile(tree: int, enable: bool) -> None:
     _check(load().wt_profile(tree, 1 if enable else 0), "wt_profile")
 
 
-def wt_profile_read(tree: int, cap: int = 64) -> list[tuple[str, float]]:
+def wt_profile_read(tree: int, cap: int = 4096) -> list[tuple[str, float]]:
     ms = np.zeros(cap, dtype=np.float32)
     kind = np.zeros(cap, dtype=np.int32)
     k = load().wt_profile_read(tree, ms.ctypes.data, kind.ctypes.data, cap)

@@ -125,15 +125,14 @@ def test_symbol_out_of_range_is_reported(wt):
 
 
 def test_lookback_timeout_is_reported_without_hanging(wt):
-    """A tile that never publishes its look-back status makes its successor's
-    bounded wait run out: the build reports WT_ERR_TIMEOUT and the GPU stays
-    usable."""
-    S = synth.uniform(8 * 4096, 256, 1, 4)
-    with wt.WaveletTree(S.size, 256, 1, tile_threads=128, spin_limit=2000,
-                        debug_skip_publish=3) as t:
+    """A block that never publishes its look-back status (node-start scan of a
+    2^16-bin histogram, 32 look-back blocks) makes its successor's bounded wait
+    run out: the build reports WT_ERR_TIMEOUT, returns, and the GPU stays usable."""
+    S = synth.uniform(50000, 65536, 2, 4)
+    with wt.WaveletTree(S.size, 65536, 2, spin_limit=2000, debug_skip_publish=3) as t:
         t.build(S)
         assert t.sync() == wt.WT_ERR_TIMEOUT
-    compare(wt, S, 256, tile_threads=128)
+    compare(wt, S, 65536)
 
 
 def test_deterministic_and_rebuildable(wt):
