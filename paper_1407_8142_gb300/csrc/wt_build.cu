@@ -239,10 +239,11 @@ __device__ __forceinline__ uint32_t count_bit(uint32_t w, uint32_t k1) {
 
 // Copy one run of `len` symbols from shared memory (byte offset soff of a
 // 16-byte aligned array) to global symbol position gpos: unaligned head and
-// tail bytes singly, the body as aligned 16-byte stores.  While copying,
-// count bit k1 of the copied symbols into cnt_a (destination tile of the
-// run's first symbol) and cnt_b (the next tile).  Writes past n are dropped
-// (reachable only after a device error).
+// tail bytes singly, the body as aligned 16-byte stores assembled from
+// aligned 16-byte shared loads (the next lane's load supplies the overhang).
+// While copying, count bit k1 of the copied symbols into cnt_a (destination
+// tile of the run's first symbol) and cnt_b (the next tile).  Writes past n
+// are dropped (reachable only after a device error).  Called by all threads.
 template <int SB, int THREADS>
 __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, uint8_t *gout,
                                          uint64_t gpos, uint32_t len, uint32_t n, uint32_t log2T,
@@ -259,7 +260,7 @@ __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, u
   const uint32_t nch = (bytes - head) >> 4;
   const uint32_t tail0 = head + (nch << 4);
   const uint32_t tail = bytes - tail0;
-  const uint32_t t = threadIdx.x;
+  const uint32_t t = threadIdx.x, lane = t & 31;
   if (t < head + tail) {
     const uint32_t o = t < head ? t : tail0 + (t - head);
     dst[o] = sb[soff + o];
@@ -273,22 +274,60 @@ __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, u
       else cnt_a += one;
     }
   }
-  for (uint32_t c = t; c < nch; c += THREADS) {
-    const uint32_t o = head + (c << 4);
-    const uint4 v = lds16_unaligned(sbase, soff + o);
-    *reinterpret_cast<uint4 *>(dst + o) = v;
-    const uint32_t ones = count_bit<SB>(v.x, k1) + count_bit<SB>(v.y, k1) +
-                          count_bit<SB>(v.z, k1) + count_bit<SB>(v.w, k1);
-    if (gpos + o / SB >= split_at) cnt_b += ones;
-    else cnt_a += ones;
+  const uint32_t a0 = soff + head;       // shared byte offset of chunk 0
+  const uint32_t aw = (a0 & ~15u) >> 2;  // its aligned 16-byte block, in words
+  const uint32_t sh = a0 & 15u;          // byte offset inside that block (run-uniform)
+  for (uint32_t cb = t - lane; cb < nch; cb += THREADS) {
+    const uint32_t c = cb + lane;
+    const bool active = c < nch;
+    uint4 cur = make_uint4(0, 0, 0, 0), v;
+    if (active) cur = *reinterpret_cast<const uint4 *>(sbase + aw + 4 * c);
+    if (sh == 0) {
+      v = cur;
+    } else {
+      uint4 nx;
+      nx.x = __shfl_down_sync(0xFFFFFFFFu, cur.x, 1);
+      nx.y = __shfl_down_sync(0xFFFFFFFFu, cur.y, 1);
+      nx.z = __shfl_down_sync(0xFFFFFFFFu, cur.z, 1);
+      nx.w = __shfl_down_sync(0xFFFFFFFFu, cur.w, 1);
+      if (lane == 31 && active) nx = *reinterpret_cast<const uint4 *>(sbase + aw + 4 * (c + 1));
+      const uint32_t r = (sh & 3u) * 8u;
+      switch (sh >> 2) {  // words [sh/4, sh/4 + 5) of cur||nx, shifted by r bits
+        case 0:
+          v = make_uint4(__funnelshift_r(cur.x, cur.y, r), __funnelshift_r(cur.y, cur.z, r),
+                         __funnelshift_r(cur.z, cur.w, r), __funnelshift_r(cur.w, nx.x, r));
+          break;
+        case 1:
+          v = make_uint4(__funnelshift_r(cur.y, cur.z, r), __funnelshift_r(cur.z, cur.w, r),
+                         __funnelshift_r(cur.w, nx.x, r), __funnelshift_r(nx.x, nx.y, r));
+          break;
+        case 2:
+          v = make_uint4(__funnelshift_r(cur.z, cur.w, r), __funnelshift_r(cur.w, nx.x, r),
+                         __funnelshift_r(nx.x, nx.y, r), __funnelshift_r(nx.y, nx.z, r));
+          break;
+        default:
+          v = make_uint4(__funnelshift_r(cur.w, nx.x, r), __funnelshift_r(nx.x, nx.y, r),
+                         __funnelshift_r(nx.y, nx.z, r), __funnelshift_r(nx.z, nx.w, r));
+          break;
+      }
+    }
+    if (active) {
+      const uint32_t o = head + (c << 4);
+      *reinterpret_cast<uint4 *>(dst + o) = v;
+      const uint32_t ones = count_bit<SB>(v.x, k1) + count_bit<SB>(v.y, k1) +
+                            count_bit<SB>(v.z, k1) + count_bit<SB>(v.w, k1);
+      if (gpos + o / SB >= split_at) cnt_b += ones;
+      else cnt_a += ones;
+    }
   }
 }
 
 template <int SB, int THREADS>
 constexpr uint32_t split_smem_bytes() {
-  // two input tiles, one output tile (+16 bytes of slack for unaligned reads),
-  // per-thread bit words and ones-prefixes, two mbarriers, run counters
-  return 3u * 32u * THREADS * SB + 16u + 8u * THREADS + 16u + 16u;
+  // two input tiles, one output tile (+32 bytes of slack for the shifted
+  // reads of copy_run), per-thread {bit word, ones-prefix}, two mbarriers,
+  // four run counters and the tile prefix
+  return 3u * 32u * THREADS * SB + 32u + 8u * THREADS + 16u + 32u;
 }
 
 template <int SB, int THREADS>
@@ -296,15 +335,16 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t TB = T * SB;
+  constexpr uint32_t G = 4 / SB;        // symbols per lane per step of pass B
+  constexpr uint32_t LPW = 32 / G;      // lanes per bitmap word in pass B
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *const sIn0 = smem;
   uint8_t *const sIn1 = smem + TB;
   uint8_t *const sOut = smem + 2 * TB;
-  uint32_t *const sWord = reinterpret_cast<uint32_t *>(smem + 3 * TB + 16);
-  uint32_t *const sPref = sWord + THREADS;
-  uint64_t *const bar = reinterpret_cast<uint64_t *>(sPref + THREADS);
-  uint32_t *const sCnt = reinterpret_cast<uint32_t *>(bar + 2);  // 4 run counters
-  __shared__ unsigned long long s_warp[33];
+  uint2 *const sWP = reinterpret_cast<uint2 *>(smem + 3 * TB + 32);  // {word, prefix}
+  uint64_t *const bar = reinterpret_cast<uint64_t *>(sWP + THREADS);
+  uint32_t *const sCnt = reinterpret_cast<uint32_t *>(bar + 2);      // 4 run counters, R
+  __shared__ uint32_t s_warp[33];
   __shared__ uint32_t s_ticket[2];
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -345,8 +385,14 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
         issue(nx, buf ^ 1);
       }
     }
-    // the tile's exclusive prefix: loads issued before waiting for the data
-    const uint32_t share = prefix_share<THREADS>(a.cin, tile);
+    // warp 0: the tile's exclusive prefix from the counts, while the copy lands
+    if (warp == 0) {
+      const uint32_t nt = prefix_terms(tile);
+      uint32_t s = 0;
+      for (uint32_t j = lane; j < nt; j += 32) s += __ldcg(prefix_term(a.cin, tile, j));
+      s = __reduce_add_sync(0xFFFFFFFFu, s);
+      if (lane == 0) sCnt[4] = s;
+    }
     const bool ok = mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, a.spin_limit, a.err);
     if (__syncthreads_or(!ok)) {
       // The copy did not land in time: wait once more (bounded) for the
@@ -368,8 +414,9 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
 
     // Pass A: 32 consecutive symbols per thread -> one bitmap word.
     const uint32_t my0 = 32 * tid;
-    uint32_t u[8 * SB];
+    uint32_t word;
     {
+      uint32_t u[8 * SB];
       const uint4 *src = reinterpret_cast<const uint4 *>(sIn + my0 * SB);
 #pragma unroll
       for (int c = 0; c < 2 * SB; ++c) {
@@ -379,46 +426,42 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
         u[4 * c + 2] = v.z;
         u[4 * c + 3] = v.w;
       }
+      word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
     }
-    const uint32_t word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
-    unsigned long long tot;
-    const uint32_t excl = (uint32_t)block_exclusive_scan64<THREADS>(
-        ((unsigned long long)share << 32) | __popc(word), s_warp, &tot);
-    const uint32_t total = (uint32_t)tot, R = (uint32_t)(tot >> 32);
-    sWord[tid] = word;
-    sPref[tid] = excl;
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
+    const uint32_t R = sCnt[4];
+    sWP[tid] = make_uint2(word, excl);
     write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, excl, total);
     __syncthreads();
 
     // Pass B: stable split of the tile into shared memory, zeros first.
-    // Warp w owns tile positions [1024w, 1024w + 1024); step q covers the
-    // 32 positions of bitmap word 32w + q, one per lane.
+    // Warp w owns tile positions [1024w, 1024w + 1024).  In step s lane i
+    // holds the G symbols at 32*G*s + G*i: one 32-bit shared load, the bits
+    // come from the bitmap word, the ones before them from word prefix +
+    // popcount of the lower bits.
     const uint32_t Zt = nv - total;
-    const uint32_t lt = lanemask_lt();
     const uint32_t seg = 1024 * warp;
-    const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
+    const uint32_t wsub = lane / LPW;
+    const uint32_t bo = (lane % LPW) * G;
+    const uint32_t lowmask = (1u << bo) - 1u;
     Sym *sOutS = reinterpret_cast<Sym *>(sOut);
-    if (seg + 1024 <= nv) {
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) {
-        const uint32_t pos = seg + 32 * q + lane;
-        const uint32_t B = sWord[32 * warp + q];
-        const uint32_t P = sPref[32 * warp + q];
-        const Sym s = sInS[pos];
-        const uint32_t r = P + __popc(B & lt);
-        const uint32_t dst = ((B >> lane) & 1u) ? Zt + r : pos - r;
-        sOutS[dst] = s;
-      }
-    } else if (seg < nv) {
-      for (int q = 0; q < 32; ++q) {
-        const uint32_t pos = seg + 32 * q + lane;
-        if (pos < nv) {
-          const uint32_t B = sWord[32 * warp + q];
-          const uint32_t P = sPref[32 * warp + q];
-          const Sym s = sInS[pos];
-          const uint32_t r = P + __popc(B & lt);
-          const uint32_t dst = ((B >> lane) & 1u) ? Zt + r : pos - r;
-          sOutS[dst] = s;
+    if (seg < nv) {
+#pragma unroll 2
+      for (uint32_t s = 0; s < 32 / G; ++s) {
+        const uint32_t pos0 = seg + 32 * G * s + G * lane;
+        const uint2 wp = sWP[32 * warp + G * s + wsub];
+        const uint32_t grp = *reinterpret_cast<const uint32_t *>(sIn + pos0 * SB);
+        const uint32_t bits = wp.x >> bo;
+        const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the tile
+        uint32_t o = Zt + Rl, z = pos0 - Rl;
+#pragma unroll
+        for (uint32_t j = 0; j < G; ++j) {
+          if (pos0 + j < nv) {
+            const Sym sym = (Sym)(grp >> (8 * SB * j));
+            if ((bits >> j) & 1u) sOutS[o++] = sym;
+            else sOutS[z++] = sym;
+          }
         }
       }
     }
@@ -426,6 +469,7 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
 
     // Phase 2: write the tile's runs to T_{l+1}, counting the next level's
     // ones per destination tile.
+    const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
     const uint32_t Zb = (uint32_t)start - R;  // zeros of level l before the tile
     const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
     const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
