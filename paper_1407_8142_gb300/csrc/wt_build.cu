@@ -281,7 +281,8 @@ __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, u
     const uint32_t c = cb + lane;
     const bool active = c < nch;
     uint4 cur = make_uint4(0, 0, 0, 0), v;
-    if (active) cur = *reinterpret_cast<const uint4 *>(sbase + aw + 4 * c);
+    // block c <= nch: the block after the last chunk supplies its overhang
+    if (c <= nch) cur = *reinterpret_cast<const uint4 *>(sbase + aw + 4 * c);
     if (sh == 0) {
       v = cur;
     } else {
