@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     const uint32_t bo = (lane % LPW) * G;
     const uint32_t lowmask = (1u << bo) - 1u;
     Sym *sOutS = reinterpret_cast<Sym *>(sOut);
-    if (seg < nv) {
-#pragma unroll 2
+    if (seg + 1024 <= nv) {
+#pragma unroll 4
       for (uint32_t s = 0; s < 32 / G; ++s) {
         const uint32_t pos0 = seg + 32 * G * s + G * lane;
         const uint2 wp = sWP[32 * warp + G * s + wsub];
@@ -458,10 +458,26 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
         uint32_t o = Zt + Rl, z = pos0 - Rl;
 #pragma unroll
         for (uint32_t j = 0; j < G; ++j) {
+          const uint32_t b = (bits >> j) & 1u;
+          sOutS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
+          o += b;
+          z += b ^ 1u;
+        }
+      }
+    } else if (seg < nv) {
+      for (uint32_t s = 0; s < 32 / G; ++s) {
+        const uint32_t pos0 = seg + 32 * G * s + G * lane;
+        const uint2 wp = sWP[32 * warp + G * s + wsub];
+        const uint32_t grp = *reinterpret_cast<const uint32_t *>(sIn + pos0 * SB);
+        const uint32_t bits = wp.x >> bo;
+        const uint32_t Rl = wp.y + __popc(wp.x & lowmask);
+        uint32_t o = Zt + Rl, z = pos0 - Rl;
+        for (uint32_t j = 0; j < G; ++j) {
           if (pos0 + j < nv) {
-            const Sym sym = (Sym)(grp >> (8 * SB * j));
-            if ((bits >> j) & 1u) sOutS[o++] = sym;
-            else sOutS[z++] = sym;
+            const uint32_t b = (bits >> j) & 1u;
+            sOutS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
+            o += b;
+            z += b ^ 1u;
           }
         }
       }
