@@ -237,21 +237,22 @@ __device__ __forceinline__ uint32_t count_bit(uint32_t w, uint32_t k1) {
   return (w >> k1) & 1u;
 }
 
-// Copy one run of `len` symbols from shared memory (byte offset soff of a
-// 16-byte aligned array) to global symbol position gpos: unaligned head and
-// tail bytes singly, the body as aligned 16-byte stores assembled from
-// aligned 16-byte shared loads (the next lane's load supplies the overhang).
-// While copying, count bit k1 of the copied symbols into cnt_a (destination
-// tile of the run's first symbol) and cnt_b (the next tile).  Writes past n
-// are dropped (reachable only after a device error).  Called by all threads.
-template <int SB, int THREADS>
-__device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, uint8_t *gout,
-                                         uint64_t gpos, uint32_t len, uint32_t n, uint32_t log2T,
-                                         uint32_t k1, uint32_t &cnt_a, uint32_t &cnt_b) {
+// Copy one run of `len` symbols, staged in shared memory at byte offset soff
+// of a 16-byte aligned word array, to global symbol position gpos; executed
+// by one warp.  Unaligned head and tail bytes are stored singly, the body as
+// aligned 16-byte stores assembled from aligned 16-byte shared loads (the next
+// lane's block supplies the overhang).  Bit k1 of the copied symbols is
+// counted into cnt_a (destination tile of position split_at - 1 or earlier)
+// and cnt_b (positions >= split_at).  Writes past n are dropped (reachable
+// only after a device error).
+template <int SB>
+__device__ __forceinline__ void warp_copy_run(const uint32_t *sbase, uint32_t soff, uint8_t *gout,
+                                              uint64_t gpos, uint32_t len, uint32_t n,
+                                              uint64_t split_at, uint32_t k1, uint32_t &cnt_a,
+                                              uint32_t &cnt_b) {
   if (gpos >= n) return;
   if (gpos + len > n) len = (uint32_t)(n - gpos);
   if (len == 0) return;
-  const uint64_t split_at = ((gpos >> log2T) + 1) << log2T;  // first position of the next tile
   uint8_t *dst = gout + gpos * SB;
   const uint32_t bytes = len * SB;
   const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbase);
@@ -260,9 +261,9 @@ __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, u
   const uint32_t nch = (bytes - head) >> 4;
   const uint32_t tail0 = head + (nch << 4);
   const uint32_t tail = bytes - tail0;
-  const uint32_t t = threadIdx.x, lane = t & 31;
-  if (t < head + tail) {
-    const uint32_t o = t < head ? t : tail0 + (t - head);
+  const uint32_t lane = threadIdx.x & 31;
+  if (lane < head + tail) {
+    const uint32_t o = lane < head ? lane : tail0 + (lane - head);
     dst[o] = sb[soff + o];
     if (o % SB == 0) {  // first byte of a symbol: count it
       uint32_t s;
@@ -277,7 +278,8 @@ __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, u
   const uint32_t a0 = soff + head;       // shared byte offset of chunk 0
   const uint32_t aw = (a0 & ~15u) >> 2;  // its aligned 16-byte block, in words
   const uint32_t sh = a0 & 15u;          // byte offset inside that block (run-uniform)
-  for (uint32_t cb = t - lane; cb < nch; cb += THREADS) {
+  const uint32_t r = (sh & 3u) * 8u;
+  for (uint32_t cb = 0; cb < nch; cb += 32) {
     const uint32_t c = cb + lane;
     const bool active = c < nch;
     uint4 cur = make_uint4(0, 0, 0, 0), v;
@@ -292,7 +294,6 @@ __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, u
       nx.z = __shfl_down_sync(0xFFFFFFFFu, cur.z, 1);
       nx.w = __shfl_down_sync(0xFFFFFFFFu, cur.w, 1);
       if (lane == 31 && active) nx = *reinterpret_cast<const uint4 *>(sbase + aw + 4 * (c + 1));
-      const uint32_t r = (sh & 3u) * 8u;
       switch (sh >> 2) {  // words [sh/4, sh/4 + 5) of cur||nx, shifted by r bits
         case 0:
           v = make_uint4(__funnelshift_r(cur.x, cur.y, r), __funnelshift_r(cur.y, cur.z, r),
@@ -323,12 +324,16 @@ __device__ __forceinline__ void copy_run(const uint32_t *sbase, uint32_t soff, u
   }
 }
 
+// per-warp staging: 1024 symbols plus 32 bytes for the shifted reads
+template <int SB>
+__host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * SB + 32u; }
+
 template <int SB, int THREADS>
 constexpr uint32_t split_smem_bytes() {
-  // two input tiles, one output tile (+32 bytes of slack for the shifted
-  // reads of copy_run), per-thread {bit word, ones-prefix}, two mbarriers,
-  // four run counters and the tile prefix
-  return 3u * 32u * THREADS * SB + 32u + 8u * THREADS + 16u + 32u;
+  // two input tiles, per-warp staging, per-thread {bit word, warp-local
+  // ones-prefix}, per-warp ones, two mbarriers, four run counters and R
+  return 2u * 32u * THREADS * SB + (THREADS / 32) * stage_bytes<SB>() + 8u * THREADS +
+         4u * (THREADS / 32) + 16u + 32u;
 }
 
 template <int SB, int THREADS>
@@ -336,16 +341,17 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t TB = T * SB;
+  constexpr uint32_t NW = THREADS / 32;
   constexpr uint32_t G = 4 / SB;        // symbols per lane per step of pass B
   constexpr uint32_t LPW = 32 / G;      // lanes per bitmap word in pass B
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *const sIn0 = smem;
   uint8_t *const sIn1 = smem + TB;
-  uint8_t *const sOut = smem + 2 * TB;
-  uint2 *const sWP = reinterpret_cast<uint2 *>(smem + 3 * TB + 32);  // {word, prefix}
-  uint64_t *const bar = reinterpret_cast<uint64_t *>(sWP + THREADS);
-  uint32_t *const sCnt = reinterpret_cast<uint32_t *>(bar + 2);      // 4 run counters, R
-  __shared__ uint32_t s_warp[33];
+  uint8_t *const sStage = smem + 2 * TB;
+  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());
+  uint32_t *const sWT = reinterpret_cast<uint32_t *>(sWP + THREADS);  // ones per warp
+  uint64_t *const bar = reinterpret_cast<uint64_t *>(sWT + NW + (NW & 1));
+  uint32_t *const sCnt = reinterpret_cast<uint32_t *>(bar + 2);       // 4 run counters, R
   __shared__ uint32_t s_ticket[2];
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -353,6 +359,8 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
   const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
   const uint32_t pshift = a.L - a.level;  // node prefix = symbol >> pshift
   const uint32_t lmask = (1u << a.L) - 1u;
+  uint8_t *const stage = sStage + warp * stage_bytes<SB>();
+  Sym *const stageS = reinterpret_cast<Sym *>(stage);
 
   auto issue = [&](uint32_t tile, int buf) {
     const uint64_t start = (uint64_t)tile * T;
@@ -413,7 +421,8 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
       __syncthreads();
     }
 
-    // Pass A: 32 consecutive symbols per thread -> one bitmap word.
+    // Pass A: 32 consecutive symbols per thread -> one bitmap word; warp scan
+    // of the ones.
     const uint32_t my0 = 32 * tid;
     uint32_t word;
     {
@@ -429,116 +438,137 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
       }
       word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
     }
-    uint32_t total;
-    const uint32_t excl = block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
-    const uint32_t R = sCnt[4];
-    sWP[tid] = make_uint2(word, excl);
-    write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, excl, total);
-    __syncthreads();
-
-    // Pass B: stable split of the tile into shared memory, zeros first.
-    // Warp w owns tile positions [1024w, 1024w + 1024).  In step s lane i
-    // holds the G symbols at 32*G*s + G*i: one 32-bit shared load, the bits
-    // come from the bitmap word, the ones before them from word prefix +
-    // popcount of the lower bits.
-    const uint32_t Zt = nv - total;
-    const uint32_t seg = 1024 * warp;
-    const uint32_t wsub = lane / LPW;
-    const uint32_t bo = (lane % LPW) * G;
-    const uint32_t lowmask = (1u << bo) - 1u;
-    Sym *sOutS = reinterpret_cast<Sym *>(sOut);
-    if (seg + 1024 <= nv) {
-#pragma unroll 4
-      for (uint32_t s = 0; s < 32 / G; ++s) {
-        const uint32_t pos0 = seg + 32 * G * s + G * lane;
-        const uint2 wp = sWP[32 * warp + G * s + wsub];
-        const uint32_t grp = *reinterpret_cast<const uint32_t *>(sIn + pos0 * SB);
-        const uint32_t bits = wp.x >> bo;
-        const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the tile
-        uint32_t o = Zt + Rl, z = pos0 - Rl;
+    const uint32_t pc = __popc(word);
+    uint32_t incl = pc;
 #pragma unroll
-        for (uint32_t j = 0; j < G; ++j) {
-          const uint32_t b = (bits >> j) & 1u;
-          sOutS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
-          o += b;
-          z += b ^ 1u;
-        }
-      }
-    } else if (seg < nv) {
-      for (uint32_t s = 0; s < 32 / G; ++s) {
-        const uint32_t pos0 = seg + 32 * G * s + G * lane;
-        const uint2 wp = sWP[32 * warp + G * s + wsub];
-        const uint32_t grp = *reinterpret_cast<const uint32_t *>(sIn + pos0 * SB);
-        const uint32_t bits = wp.x >> bo;
-        const uint32_t Rl = wp.y + __popc(wp.x & lowmask);
-        uint32_t o = Zt + Rl, z = pos0 - Rl;
-        for (uint32_t j = 0; j < G; ++j) {
-          if (pos0 + j < nv) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    const uint32_t pw = incl - pc;                 // ones before this word, within the warp
+    sWP[tid] = make_uint2(word, pw);
+    if (lane == 31) sWT[warp] = incl;
+    __syncthreads();
+    const uint32_t wt = lane < NW ? sWT[lane] : 0u;
+    const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wt : 0u);  // ones before the warp
+    const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wt);
+    const uint32_t R = sCnt[4];
+    write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + pw, total);
+
+    // Pass B: stable split of the warp's segment into its staging area,
+    // zeros first.  In step s lane i holds the G symbols at 32*G*s + G*i:
+    // one 32-bit shared load; their bits come from the bitmap word, the ones
+    // before them from the word prefix plus a popcount.
+    const uint32_t seg = 1024 * warp;
+    const uint32_t nvw = nv > seg ? min(nv - seg, 1024u) : 0u;  // symbols of this warp
+    const uint32_t tw = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t nzw = nvw - tw;                              // zeros of this warp
+    if (nvw) {
+      const uint32_t wsub = lane / LPW;
+      const uint32_t bo = (lane % LPW) * G;
+      const uint32_t lowmask = (1u << bo) - 1u;
+      const uint8_t *segIn = sIn + seg * SB;
+      if (nvw == 1024) {
+#pragma unroll 4
+        for (uint32_t s = 0; s < 32 / G; ++s) {
+          const uint32_t pos0 = 32 * G * s + G * lane;
+          const uint2 wp = sWP[32 * warp + G * s + wsub];
+          const uint32_t grp = *reinterpret_cast<const uint32_t *>(segIn + pos0 * SB);
+          const uint32_t bits = wp.x >> bo;
+          const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the warp
+          uint32_t o = nzw + Rl, z = pos0 - Rl;
+#pragma unroll
+          for (uint32_t j = 0; j < G; ++j) {
             const uint32_t b = (bits >> j) & 1u;
-            sOutS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
+            stageS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
             o += b;
             z += b ^ 1u;
           }
         }
-      }
-    }
-    __syncthreads();
-
-    // Phase 2: write the tile's runs to T_{l+1}, counting the next level's
-    // ones per destination tile.
-    const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
-    const uint32_t Zb = (uint32_t)start - R;  // zeros of level l before the tile
-    const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
-    const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
-    if (pf == pl) {
-      // the whole tile lies in one node: one run of zeros, one run of ones
-      const uint2 tb = __ldg(&a.tab[pf]);
-      const uint32_t *sO = reinterpret_cast<const uint32_t *>(sOut);
-      uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
-      const uint64_t g0 = (uint64_t)tb.x + Zb, g1 = (uint64_t)tb.y + R;
-      copy_run<SB, THREADS>(sO, 0, a.out, g0, Zt, a.n, a.log2T, k1, c0a, c0b);
-      copy_run<SB, THREADS>(sO, Zt * SB, a.out, g1, nv - Zt, a.n, a.log2T, k1, c1a, c1b);
-      const uint32_t v0 = __reduce_add_sync(0xFFFFFFFFu, c0a);
-      const uint32_t v1 = __reduce_add_sync(0xFFFFFFFFu, c0b);
-      const uint32_t v2 = __reduce_add_sync(0xFFFFFFFFu, c1a);
-      const uint32_t v3 = __reduce_add_sync(0xFFFFFFFFu, c1b);
-      if (lane == 0) {
-        if (v0) atomicAdd(&sCnt[0], v0);
-        if (v1) atomicAdd(&sCnt[1], v1);
-        if (v2) atomicAdd(&sCnt[2], v2);
-        if (v3) atomicAdd(&sCnt[3], v3);
-      }
-      __syncthreads();
-      if (tid < 4) {
-        const uint32_t v = sCnt[tid];
-        sCnt[tid] = 0;
-        const uint64_t g = tid < 2 ? g0 : g1;
-        const uint64_t dt = (g >> a.log2T) + (tid & 1);
-        if (v && dt < a.NT) counts_add(a.cout, (uint32_t)dt, v);
-      }
-    } else {
-      Sym *outS = reinterpret_cast<Sym *>(a.out);
-      for (uint32_t base = 0; base < nv; base += THREADS) {
-        const uint32_t kk = base + tid;
-        const bool valid = kk < nv;
-        uint32_t dest = 0xFFFFFFFFu, bit = 0;
-        if (valid) {
-          const Sym s = sOutS[kk];
-          const uint32_t p = ((uint32_t)s & lmask) >> pshift;
-          const uint2 tb = __ldg(&a.tab[p]);
-          dest = kk < Zt ? tb.x + Zb + kk : tb.y + R + (kk - Zt);
-          if (dest < a.n) outS[dest] = s;
-          else dest = 0xFFFFFFFFu;
-          bit = ((uint32_t)s >> k1) & 1u;
+      } else {
+        for (uint32_t s = 0; s < 32 / G; ++s) {
+          const uint32_t pos0 = 32 * G * s + G * lane;
+          const uint2 wp = sWP[32 * warp + G * s + wsub];
+          const uint32_t grp = *reinterpret_cast<const uint32_t *>(segIn + pos0 * SB);
+          const uint32_t bits = wp.x >> bo;
+          const uint32_t Rl = wp.y + __popc(wp.x & lowmask);
+          uint32_t o = nzw + Rl, z = pos0 - Rl;
+          for (uint32_t j = 0; j < G; ++j) {
+            if (pos0 + j < nvw) {
+              const uint32_t b = (bits >> j) & 1u;
+              stageS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
+              o += b;
+              z += b ^ 1u;
+            }
+          }
         }
-        const uint32_t dt = dest >> a.log2T;
-        const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit && dest != 0xFFFFFFFFu);
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dt);
-        const uint32_t c = __popc(ones & peers);
-        if (dest != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1) && c) counts_add(a.cout, dt, c);
+      }
+      __syncwarp();
+
+      // Phase 2: the warp writes its zeros and ones to T_{l+1}, counting the
+      // next level's ones per destination tile.
+      const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
+      const uint32_t Zw = (uint32_t)start - R + seg - Pw;  // zeros of level l before the warp
+      const uint32_t Ow = R + Pw;                          // ones of level l before the warp
+      const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
+      const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
+      if (pf == pl) {
+        // the whole tile lies in one node: its zeros and ones are two runs
+        const uint2 tb = __ldg(&a.tab[pf]);
+        const uint32_t *sO = reinterpret_cast<const uint32_t *>(stage);
+        const uint64_t r0 = (uint64_t)tb.x + (uint32_t)start - R;  // run starts
+        const uint64_t r1 = (uint64_t)tb.y + R;
+        const uint64_t s0 = ((r0 >> a.log2T) + 1) << a.log2T, s1 = ((r1 >> a.log2T) + 1) << a.log2T;
+        uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
+        warp_copy_run<SB>(sO, 0, a.out, (uint64_t)tb.x + Zw, nzw, a.n, s0, k1, c0a, c0b);
+        warp_copy_run<SB>(sO, nzw * SB, a.out, (uint64_t)tb.y + Ow, tw, a.n, s1, k1, c1a, c1b);
+        const uint32_t v0 = __reduce_add_sync(0xFFFFFFFFu, c0a);
+        const uint32_t v1 = __reduce_add_sync(0xFFFFFFFFu, c0b);
+        const uint32_t v2 = __reduce_add_sync(0xFFFFFFFFu, c1a);
+        const uint32_t v3 = __reduce_add_sync(0xFFFFFFFFu, c1b);
+        if (lane == 0) {
+          if (v0) atomicAdd(&sCnt[0], v0);
+          if (v1) atomicAdd(&sCnt[1], v1);
+          if (v2) atomicAdd(&sCnt[2], v2);
+          if (v3) atomicAdd(&sCnt[3], v3);
+        }
+      } else {
+        Sym *outS = reinterpret_cast<Sym *>(a.out);
+        for (uint32_t base = 0; base < nvw; base += 32) {
+          const uint32_t kk = base + lane;
+          const bool valid = kk < nvw;
+          uint32_t dest = 0xFFFFFFFFu, bit = 0;
+          if (valid) {
+            const Sym s = stageS[kk];
+            const uint32_t p = ((uint32_t)s & lmask) >> pshift;
+            const uint2 tb = __ldg(&a.tab[p]);
+            dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
+            if (dest < a.n) outS[dest] = s;
+            else dest = 0xFFFFFFFFu;
+            bit = ((uint32_t)s >> k1) & 1u;
+          }
+          const uint32_t dt = dest >> a.log2T;
+          const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit && dest != 0xFFFFFFFFu);
+          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dt);
+          const uint32_t c = __popc(ones & peers);
+          if (dest != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1) && c)
+            counts_add(a.cout, dt, c);
+        }
       }
     }
     __syncthreads();
+    if (tid < 4) {
+      const uint32_t v = sCnt[tid];
+      if (v) {
+        // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
+        const uint32_t pf = ((uint32_t)reinterpret_cast<const Sym *>(sIn)[0] & lmask) >> pshift;
+        const uint2 tb = __ldg(&a.tab[pf]);
+        const uint64_t g = tid < 2 ? (uint64_t)tb.x + (uint32_t)start - R : (uint64_t)tb.y + R;
+        const uint64_t dt = (g >> a.log2T) + (tid & 1);
+        sCnt[tid] = 0;
+        if (dt < a.NT) counts_add(a.cout, (uint32_t)dt, v);
+      }
+    }
   }
 }
 
