@@ -105,67 +105,221 @@ __device__ __forceinline__ void write_level(const LevelOut &o, uint32_t tile, ui
   }
 }
 
+// ------------------------------------------------------------------ tile pipeline
+// Every level pass runs persistent CTAs that take tiles of T = 32*THREADS
+// symbols by ticket.  Tickets are fetched two tiles ahead, a tile's symbols
+// are copied into shared memory by the TMA engine one tile ahead (double
+// buffer), and the loads of a tile's count prefix are issued one tile ahead,
+// so no round trip to memory sits between two tiles of a CTA.
+template <int SB, int THREADS>
+struct TilePipe {
+  static constexpr uint32_t T = 32 * THREADS;
+  static constexpr uint32_t TB = T * SB;
+  uint8_t *sIn0, *sIn1;
+  uint64_t *bar;       // 2 mbarriers
+  uint32_t *ring;      // 3 tickets
+  const uint8_t *in;   // this level's symbols, 16-byte aligned
+  int in_padded;       // in holds whole tiles -> copy whole tiles
+  uint32_t n, NT;
+  uint32_t *ticket;
+
+  __device__ __forceinline__ void issue(uint32_t tile, int buf) const {
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, n - start);
+    const uint32_t bytes = in_padded ? TB : ((nv * SB) & ~15u);
+    mbar_arrive_expect_tx(&bar[buf], bytes);
+    if (bytes) bulk_g2s(buf ? sIn1 : sIn0, in + start * SB, bytes, &bar[buf]);
+  }
+  // thread 0, before the first __syncthreads
+  __device__ __forceinline__ void prologue() const {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    const uint32_t t0 = atomicAdd(ticket, 1u);
+    const uint32_t t1 = atomicAdd(ticket, 1u);
+    ring[0] = t0;
+    ring[1] = t1;
+    if (t0 < NT) issue(t0, 0);
+  }
+  // thread 0 at the top of iteration `it`: fetch the ticket of tile it+2
+  // (returned, stored at the end of the iteration) and start the copy of
+  // tile it+1
+  __device__ __forceinline__ uint32_t advance(uint32_t it, uint32_t nxt) const {
+    const uint32_t nn = atomicAdd(ticket, 1u);
+    if (nxt < NT) {
+      fence_proxy_async_smem();
+      issue(nxt, (it + 1) & 1);
+    }
+    return nn;
+  }
+  // all threads: wait for tile `it`'s symbols (bounded); false on timeout
+  __device__ __forceinline__ bool wait(uint32_t it, uint32_t spin, int *err) const {
+    return mbar_wait_bounded(&bar[it & 1], (it >> 1) & 1u, spin, err);
+  }
+  // after a timeout: wait (bounded) for the copies this CTA started
+  __device__ __forceinline__ void drain(uint32_t it, uint32_t spin, int *err) const {
+    if (threadIdx.x == 0) {
+      mbar_wait_bounded(&bar[it & 1], (it >> 1) & 1u, spin, err);
+      if (ring[(it + 1) % 3] < NT) mbar_wait_bounded(&bar[(it + 1) & 1], ((it + 1) >> 1) & 1u, spin, err);
+    }
+  }
+  __device__ __forceinline__ uint8_t *data(uint32_t it) const { return (it & 1) ? sIn1 : sIn0; }
+  // tail bytes of an unpadded input that the bulk copy (multiple of 16 bytes) left out
+  __device__ __forceinline__ bool fill_tail(uint8_t *sIn, uint64_t start, uint32_t nv) const {
+    if (in_padded || ((nv * SB) & 15u) == 0) return false;
+    for (uint32_t i = ((nv * SB) & ~15u) + threadIdx.x; i < nv * SB; i += THREADS)
+      sIn[i] = in[start * SB + i];
+    return true;
+  }
+};
+
+// This thread's part of the count-prefix of `tile`, loads issued now and
+// summed later (up to 3 terms per thread: tile < 2^20 and THREADS >= 128).
+struct PrefixLoads {
+  uint32_t v0, v1, v2;
+  __device__ __forceinline__ uint32_t sum() const { return v0 + v1 + v2; }
+};
+
+template <int THREADS>
+__device__ __forceinline__ PrefixLoads prefix_loads(const TileCounts &c, uint32_t tile, uint32_t NT) {
+  PrefixLoads p{0, 0, 0};
+  if (tile >= NT) return p;
+  const uint32_t nt = prefix_terms(tile), j = threadIdx.x;
+  if (j < nt) p.v0 = __ldcg(prefix_term(c, tile, j));
+  if (j + THREADS < nt) p.v1 = __ldcg(prefix_term(c, tile, j + THREADS));
+  if (j + 2 * THREADS < nt) p.v2 = __ldcg(prefix_term(c, tile, j + 2 * THREADS));
+  return p;
+}
+
+template <int SB, int THREADS>
+__device__ __forceinline__ void load_from_smem(const uint8_t *sIn, uint32_t my0, uint32_t *u) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(sIn + my0 * SB);
+#pragma unroll
+  for (int c = 0; c < 2 * SB; ++c) {
+    const uint4 v = src[c];
+    u[4 * c + 0] = v.x;
+    u[4 * c + 1] = v.y;
+    u[4 * c + 2] = v.z;
+    u[4 * c + 3] = v.w;
+  }
+}
+
+template <int SB, int THREADS>
+constexpr uint32_t pipe_smem_bytes() {
+  return 2u * 32u * THREADS * SB;
+}
+
 // ------------------------------------------------------------------ pre-pass
 struct PrepassArgs {
   const uint8_t *in;  // S, 16-byte aligned
+  int in_padded;
   uint32_t n, L, NT, sigma;
   uint32_t *hist;     // 2^L bins
   TileCounts cnt;     // level-0 ones per tile
   uint32_t *ticket;
+  uint32_t spin_limit;
   int *err;
 };
 
+template <int SB, int THREADS>
+constexpr uint32_t prepass_smem_bytes(uint32_t hist_bins) {
+  return pipe_smem_bytes<SB, THREADS>() + 4u * hist_bins + 64u;
+}
+
 // Reads S once: the 2^L-bin histogram (node sizes of every level), the range
-// check, and the level-0 ones of every tile.  Persistent CTAs, tiles by ticket.
+// check, and the level-0 ones of every tile.
 template <int SB, int THREADS, bool HIST_SMEM>
 __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
   constexpr uint32_t T = 32 * THREADS;
-  extern __shared__ __align__(16) uint32_t s_hist[];
-  __shared__ uint32_t s_warp[33];
-  __shared__ uint32_t s_tile;
-  const uint32_t tid = threadIdx.x, lane = tid & 31;
-  const uint32_t lmask = (1u << a.L) - 1u;
+  constexpr uint32_t NW = THREADS / 32;
+  extern __shared__ __align__(128) uint8_t smem[];
+  TilePipe<SB, THREADS> pipe;
   const uint32_t nbins = 1u << a.L;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint32_t *const s_hist = reinterpret_cast<uint32_t *>(smem + 2 * pipe.TB);
+  uint64_t *const bar = reinterpret_cast<uint64_t *>(s_hist + (HIST_SMEM ? ((nbins + 1) & ~1u) : 0));
+  pipe.bar = bar;
+  pipe.ring = reinterpret_cast<uint32_t *>(bar + 2);
+  uint32_t *const s_wt = pipe.ring + 4;  // ones per warp
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lmask = nbins - 1u;
   uint32_t bad = 0;
   if (HIST_SMEM)
     for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
+  if (tid == 0) pipe.prologue();
+  __syncthreads();
 
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = pipe.ring[it % 3];
     if (tile >= a.NT) break;
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = pipe.advance(it, nxt);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
+    if (__syncthreads_or(!ok)) {
+      pipe.drain(it, a.spin_limit, a.err);
+      __syncthreads();
+      break;
+    }
     const uint64_t start = (uint64_t)tile * T;
     const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
     const uint32_t my0 = 32 * tid;
     uint32_t u[8 * SB];
-    load32<SB>(a.in + (start + my0) * SB, my0, nv, u);
+    load_from_smem<SB, THREADS>(sIn, my0, u);
     const uint32_t word = a.L ? pack_bits<SB>(u, a.L - 1) & valid_mask(my0, nv) : 0u;
-#pragma unroll 4
-    for (int q = 0; q < 32; ++q) {
-      const bool valid = my0 + q < nv;
-      const uint32_t s = symbol_at<SB>(u, q);
-      if (valid) bad |= (uint32_t)(s >= a.sigma);
-      if (HIST_SMEM) {
-        if (valid) atomicAdd(&s_hist[s & lmask], 1u);
-      } else {
-        const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
-        if (valid) {
+    if (my0 + 32 <= nv) {
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) {
+        const uint32_t s = symbol_at<SB>(u, q);
+        bad |= (uint32_t)(s >= a.sigma);
+        if (HIST_SMEM) {
+          atomicAdd(&s_hist[s & lmask], 1u);
+        } else {
           const uint32_t v = s & lmask;
-          const uint32_t peers = __match_any_sync(am, v);
+          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, v);
           if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
         }
       }
-    }
-    uint32_t total;
-    block_exclusive_scan<THREADS>(__popc(word), s_warp, &total);
-    if (tid == 0 && a.L) {
-      a.cnt.c0[tile] = total;
-      if (total) {
-        atomicAdd(&a.cnt.c1[tile >> 6], total);
-        atomicAdd(&a.cnt.c2[tile >> 12], total);
+    } else {
+      for (int q = 0; q < 32; ++q) {
+        const bool valid = my0 + q < nv;
+        const uint32_t s = symbol_at<SB>(u, q);
+        if (valid) bad |= (uint32_t)(s >= a.sigma);
+        if (HIST_SMEM) {
+          if (valid) atomicAdd(&s_hist[s & lmask], 1u);
+        } else {
+          const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
+          if (valid) {
+            const uint32_t v = s & lmask;
+            const uint32_t peers = __match_any_sync(am, v);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
+          }
+        }
       }
     }
+    const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, __popc(word));
+    if (lane == 0) s_wt[warp] = wsum;
+    __syncthreads();
+    if (warp == 0 && a.L) {
+      const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, lane < NW ? s_wt[lane] : 0u);
+      if (lane == 0) {
+        a.cnt.c0[tile] = total;
+        if (total) {
+          atomicAdd(&a.cnt.c1[tile >> 6], total);
+          atomicAdd(&a.cnt.c2[tile >> 12], total);
+        }
+      }
+    }
+    if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
+    __syncthreads();
   }
   if (bad) latch_error(a.err, WT_ERR_SYMBOL);
   if (HIST_SMEM) {
@@ -178,38 +332,83 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
 // ------------------------------------------------------------------ last level
 struct LeafArgs {
   const uint8_t *in;  // T_{L-1}, 16-byte aligned
+  int in_padded;
   uint32_t n, L, NT, NB;
   uint64_t W;
   LevelOut out;
   TileCounts cnt;     // ones of this level per tile
   uint32_t *ticket;
+  uint32_t spin_limit;
+  int *err;
 };
+
+template <int SB, int THREADS>
+constexpr uint32_t leaf_smem_bytes() {
+  return pipe_smem_bytes<SB, THREADS>() + 8u * (THREADS / 32) + 64u;
+}
 
 // Level L-1 (and level 0 when L = 1): bits and directory; its nodes have
 // range 2 and no children.
 template <int SB, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_leaf(LeafArgs a) {
   constexpr uint32_t T = 32 * THREADS;
-  __shared__ unsigned long long s_warp[33];
-  __shared__ uint32_t s_tile;
-  const uint32_t tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
+  constexpr uint32_t NW = THREADS / 32;
+  extern __shared__ __align__(128) uint8_t smem[];
+  TilePipe<SB, THREADS> pipe;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint2 *const s_wt = reinterpret_cast<uint2 *>(smem + 2 * pipe.TB);  // {ones, prefix share} per warp
+  pipe.bar = reinterpret_cast<uint64_t *>(s_wt + NW);
+  pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) pipe.prologue();
+  __syncthreads();
+  PrefixLoads pre = prefix_loads<THREADS>(a.cnt, pipe.ring[0], a.NT);
+
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = pipe.ring[it % 3];
     if (tile >= a.NT) break;
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = pipe.advance(it, nxt);
+    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cnt, nxt, a.NT);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
+    if (__syncthreads_or(!ok)) {
+      pipe.drain(it, a.spin_limit, a.err);
+      __syncthreads();
+      break;
+    }
     const uint64_t start = (uint64_t)tile * T;
     const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
     const uint32_t my0 = 32 * tid;
-    const uint32_t share = prefix_share<THREADS>(a.cnt, tile);
     uint32_t u[8 * SB];
-    load32<SB>(a.in + (start + my0) * SB, my0, nv, u);
+    load_from_smem<SB, THREADS>(sIn, my0, u);
     const uint32_t word = pack_bits<SB>(u, 0) & valid_mask(my0, nv);
-    unsigned long long tot;
-    const unsigned long long ex =
-        block_exclusive_scan64<THREADS>(((unsigned long long)share << 32) | __popc(word), s_warp, &tot);
-    write_level<THREADS>(a.out, tile, a.NT, start, my0, a.n, a.NB, a.W, word,
-                         (uint32_t)(tot >> 32), (uint32_t)ex, (uint32_t)tot);
+    const uint32_t pc = __popc(word);
+    uint32_t incl = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, pre.sum());
+    if (lane == 31) s_wt[warp] = make_uint2(incl, share);
+    __syncthreads();
+    const uint2 wv = lane < NW ? s_wt[lane] : make_uint2(0, 0);
+    const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);
+    const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
+    const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);
+    write_level<THREADS>(a.out, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + incl - pc, total);
+    if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
+    pre = pre_next;
+    __syncthreads();
   }
 }
 
@@ -217,7 +416,7 @@ __global__ void __launch_bounds__(THREADS) k_leaf(LeafArgs a) {
 struct SplitArgs {
   const uint8_t *in;   // T_l, 16-byte aligned
   uint8_t *out;        // T_{l+1}
-  int in_padded;       // in holds whole tiles (scratch buffer) -> copy full tiles
+  int in_padded;       // in holds whole tiles (scratch buffer) -> copy whole tiles
   uint32_t n, L, level, NT, NB, log2T;
   uint64_t W;
   const uint2 *tab;    // this level's {O_l[p], E_{l+1}[2p+1] - O_l[p]}
@@ -328,98 +527,77 @@ __device__ __forceinline__ void warp_copy_run(const uint32_t *sbase, uint32_t so
 template <int SB>
 __host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * SB + 32u; }
 
+constexpr uint32_t kTabSmem = 1024;  // level tables up to this many nodes live in shared memory
+
 template <int SB, int THREADS>
 constexpr uint32_t split_smem_bytes() {
   // two input tiles, per-warp staging, per-thread {bit word, warp-local
-  // ones-prefix}, per-warp ones, two mbarriers, four run counters and R
-  return 2u * 32u * THREADS * SB + (THREADS / 32) * stage_bytes<SB>() + 8u * THREADS +
-         4u * (THREADS / 32) + 16u + 32u;
+  // ones-prefix}, per-warp {ones, prefix share}, the level table, mbarriers,
+  // tickets, run counters and run starts
+  return pipe_smem_bytes<SB, THREADS>() + (THREADS / 32) * stage_bytes<SB>() + 8u * THREADS +
+         8u * (THREADS / 32) + 8u * kTabSmem + 128u;
 }
 
 template <int SB, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t T = 32 * THREADS;
-  constexpr uint32_t TB = T * SB;
   constexpr uint32_t NW = THREADS / 32;
   constexpr uint32_t G = 4 / SB;        // symbols per lane per step of pass B
   constexpr uint32_t LPW = 32 / G;      // lanes per bitmap word in pass B
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *const sIn0 = smem;
-  uint8_t *const sIn1 = smem + TB;
-  uint8_t *const sStage = smem + 2 * TB;
-  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());
-  uint32_t *const sWT = reinterpret_cast<uint32_t *>(sWP + THREADS);  // ones per warp
-  uint64_t *const bar = reinterpret_cast<uint64_t *>(sWT + NW + (NW & 1));
-  uint32_t *const sCnt = reinterpret_cast<uint32_t *>(bar + 2);       // 4 run counters, R
-  __shared__ uint32_t s_ticket[2];
+  TilePipe<SB, THREADS> pipe;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint8_t *const sStage = smem + 2 * pipe.TB;
+  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());  // {word, prefix}
+  uint2 *const sWT = sWP + THREADS;                  // per warp {ones, prefix share}
+  uint2 *const sTab = sWT + NW;                      // level table (small levels)
+  pipe.bar = reinterpret_cast<uint64_t *>(sTab + kTabSmem);
+  pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
+  uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
+  unsigned long long *const sRun = reinterpret_cast<unsigned long long *>(sCnt + 4);  // 2 run starts
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t k = a.L - 1 - a.level;   // bit of this level
   const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
   const uint32_t pshift = a.L - a.level;  // node prefix = symbol >> pshift
   const uint32_t lmask = (1u << a.L) - 1u;
+  const uint32_t nodes = 1u << a.level;
+  const bool tab_smem = nodes <= kTabSmem;
+  const uint2 *const tab = tab_smem ? sTab : a.tab;
   uint8_t *const stage = sStage + warp * stage_bytes<SB>();
   Sym *const stageS = reinterpret_cast<Sym *>(stage);
 
-  auto issue = [&](uint32_t tile, int buf) {
-    const uint64_t start = (uint64_t)tile * T;
-    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
-    const uint32_t bytes = a.in_padded ? TB : ((nv * SB) & ~15u);
-    mbar_arrive_expect_tx(&bar[buf], bytes);
-    if (bytes) bulk_g2s(buf ? sIn1 : sIn0, a.in + start * SB, bytes, &bar[buf]);
-  };
-
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-    const uint32_t t0 = atomicAdd(a.ticket, 1u);
-    s_ticket[0] = t0;
-    if (t0 < a.NT) issue(t0, 0);
-  }
+  if (tab_smem)
+    for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
   if (tid < 4) sCnt[tid] = 0;
+  if (tid == 0) pipe.prologue();
   __syncthreads();
+  PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
 
   for (uint32_t it = 0;; ++it) {
-    const int buf = it & 1;
-    const uint32_t tile = s_ticket[buf];
+    const uint32_t tile = pipe.ring[it % 3];
     if (tile >= a.NT) break;
-    uint8_t *const sIn = buf ? sIn1 : sIn0;
-    if (tid == 0) {
-      const uint32_t nx = atomicAdd(a.ticket, 1u);
-      s_ticket[buf ^ 1] = nx;
-      if (nx < a.NT) {
-        fence_proxy_async_smem();
-        issue(nx, buf ^ 1);
-      }
-    }
-    // warp 0: the tile's exclusive prefix from the counts, while the copy lands
-    if (warp == 0) {
-      const uint32_t nt = prefix_terms(tile);
-      uint32_t s = 0;
-      for (uint32_t j = lane; j < nt; j += 32) s += __ldcg(prefix_term(a.cin, tile, j));
-      s = __reduce_add_sync(0xFFFFFFFFu, s);
-      if (lane == 0) sCnt[4] = s;
-    }
-    const bool ok = mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, a.spin_limit, a.err);
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = pipe.advance(it, nxt);
+    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
     if (__syncthreads_or(!ok)) {
-      // The copy did not land in time: wait once more (bounded) for the
-      // copies this CTA started, then stop.
-      if (tid == 0) {
-        mbar_wait_bounded(&bar[buf], (it >> 1) & 1u, a.spin_limit, a.err);
-        mbar_wait_bounded(&bar[buf ^ 1], ((it + 1) >> 1) & 1u, a.spin_limit, a.err);
-      }
+      pipe.drain(it, a.spin_limit, a.err);
       __syncthreads();
-      return;
+      break;
     }
     const uint64_t start = (uint64_t)tile * T;
     const uint32_t nv = (uint32_t)umin64(T, a.n - start);
-    if (!a.in_padded && ((nv * SB) & 15u)) {  // tail bytes of an unpadded input
-      for (uint32_t i = ((nv * SB) & ~15u) + tid; i < nv * SB; i += THREADS)
-        sIn[i] = a.in[start * SB + i];
-      __syncthreads();
-    }
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
 
     // Pass A: 32 consecutive symbols per thread -> one bitmap word; warp scan
     // of the ones.
@@ -427,15 +605,7 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     uint32_t word;
     {
       uint32_t u[8 * SB];
-      const uint4 *src = reinterpret_cast<const uint4 *>(sIn + my0 * SB);
-#pragma unroll
-      for (int c = 0; c < 2 * SB; ++c) {
-        const uint4 v = src[c];
-        u[4 * c + 0] = v.x;
-        u[4 * c + 1] = v.y;
-        u[4 * c + 2] = v.z;
-        u[4 * c + 3] = v.w;
-      }
+      load_from_smem<SB, THREADS>(sIn, my0, u);
       word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
     }
     const uint32_t pc = __popc(word);
@@ -445,14 +615,15 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
       const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
       if (lane >= (uint32_t)o) incl += y;
     }
-    const uint32_t pw = incl - pc;                 // ones before this word, within the warp
+    const uint32_t pw = incl - pc;  // ones before this word, within the warp
     sWP[tid] = make_uint2(word, pw);
-    if (lane == 31) sWT[warp] = incl;
+    const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, pre.sum());
+    if (lane == 31) sWT[warp] = make_uint2(incl, share);
     __syncthreads();
-    const uint32_t wt = lane < NW ? sWT[lane] : 0u;
-    const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wt : 0u);  // ones before the warp
-    const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wt);
-    const uint32_t R = sCnt[4];
+    const uint2 wv = lane < NW ? sWT[lane] : make_uint2(0, 0);
+    const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);  // ones before the warp
+    const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
+    const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);                       // ones before the tile
     write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + pw, total);
 
     // Pass B: stable split of the warp's segment into its staging area,
@@ -463,6 +634,10 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     const uint32_t nvw = nv > seg ? min(nv - seg, 1024u) : 0u;  // symbols of this warp
     const uint32_t tw = __shfl_sync(0xFFFFFFFFu, incl, 31);
     const uint32_t nzw = nvw - tw;                              // zeros of this warp
+    const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
+    const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
+    const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
+    const uint32_t Zb = (uint32_t)start - R;  // zeros of level l before the tile
     if (nvw) {
       const uint32_t wsub = lane / LPW;
       const uint32_t bo = (lane % LPW) * G;
@@ -507,16 +682,13 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
 
       // Phase 2: the warp writes its zeros and ones to T_{l+1}, counting the
       // next level's ones per destination tile.
-      const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
-      const uint32_t Zw = (uint32_t)start - R + seg - Pw;  // zeros of level l before the warp
-      const uint32_t Ow = R + Pw;                          // ones of level l before the warp
-      const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
-      const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
+      const uint32_t Zw = Zb + seg - Pw;  // zeros of level l before the warp
+      const uint32_t Ow = R + Pw;         // ones of level l before the warp
       if (pf == pl) {
         // the whole tile lies in one node: its zeros and ones are two runs
-        const uint2 tb = __ldg(&a.tab[pf]);
+        const uint2 tb = tab[pf];
         const uint32_t *sO = reinterpret_cast<const uint32_t *>(stage);
-        const uint64_t r0 = (uint64_t)tb.x + (uint32_t)start - R;  // run starts
+        const uint64_t r0 = (uint64_t)tb.x + Zb;  // run starts
         const uint64_t r1 = (uint64_t)tb.y + R;
         const uint64_t s0 = ((r0 >> a.log2T) + 1) << a.log2T, s1 = ((r1 >> a.log2T) + 1) << a.log2T;
         uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
@@ -531,6 +703,10 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
           if (v1) atomicAdd(&sCnt[1], v1);
           if (v2) atomicAdd(&sCnt[2], v2);
           if (v3) atomicAdd(&sCnt[3], v3);
+          if (warp == 0) {
+            sRun[0] = r0;
+            sRun[1] = r1;
+          }
         }
       } else {
         Sym *outS = reinterpret_cast<Sym *>(a.out);
@@ -541,7 +717,7 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
           if (valid) {
             const Sym s = stageS[kk];
             const uint32_t p = ((uint32_t)s & lmask) >> pshift;
-            const uint2 tb = __ldg(&a.tab[p]);
+            const uint2 tb = tab[p];
             dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
             if (dest < a.n) outS[dest] = s;
             else dest = 0xFFFFFFFFu;
@@ -556,16 +732,15 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
         }
       }
     }
+    if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
+    pre = pre_next;
     __syncthreads();
-    if (tid < 4) {
+    if (tid < 4 && pf == pl) {
+      // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
       const uint32_t v = sCnt[tid];
       if (v) {
-        // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
-        const uint32_t pf = ((uint32_t)reinterpret_cast<const Sym *>(sIn)[0] & lmask) >> pshift;
-        const uint2 tb = __ldg(&a.tab[pf]);
-        const uint64_t g = tid < 2 ? (uint64_t)tb.x + (uint32_t)start - R : (uint64_t)tb.y + R;
-        const uint64_t dt = (g >> a.log2T) + (tid & 1);
         sCnt[tid] = 0;
+        const uint64_t dt = (sRun[tid >> 1] >> a.log2T) + (tid & 1);
         if (dt < a.NT) counts_add(a.cout, (uint32_t)dt, v);
       }
     }
@@ -753,11 +928,19 @@ struct Launcher {
   }
 };
 
+template <typename K>
+int set_smem(K kern, size_t bytes) {
+  if (bytes > 48 * 1024)
+    WT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return WT_OK;
+}
+
 template <int SB, int THREADS>
-int launch_prepass(Launcher &ln, const uint8_t *in) {
+int launch_prepass(Launcher &ln, const uint8_t *in, bool in_padded) {
   wt_tree *t = ln.t;
   PrepassArgs a;
   a.in = in;
+  a.in_padded = in_padded ? 1 : 0;
   a.n = (uint32_t)t->n;
   a.L = t->L;
   a.NT = (uint32_t)t->NT;
@@ -765,18 +948,22 @@ int launch_prepass(Launcher &ln, const uint8_t *in) {
   a.hist = t->d_hist;
   a.cnt = ln.counts(0);
   a.ticket = ln.ticket();
+  a.spin_limit = ln.spin();
   a.err = ln.err();
   const uint32_t nbins = 1u << t->L;
   ln.before(kPrepass);
   if (nbins <= kHistSmemMaxBins) {
     auto kern = k_prepass<SB, THREADS, true>;
-    const size_t sm = nbins * sizeof(uint32_t);
+    const size_t sm = prepass_smem_bytes<SB, THREADS>(nbins);
+    if (int rc = set_smem(kern, sm)) return rc;
     const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
     kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
   } else {
     auto kern = k_prepass<SB, THREADS, false>;
-    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, 0, t->sms, t->cfg.ctas_per_sm));
-    kern<<<std::max(grid, 1), THREADS, 0, ln.st>>>(a);
+    const size_t sm = prepass_smem_bytes<SB, THREADS>(0);
+    if (int rc = set_smem(kern, sm)) return rc;
+    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
+    kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
   }
   ln.after();
   ++ln.pass;
@@ -785,10 +972,11 @@ int launch_prepass(Launcher &ln, const uint8_t *in) {
 }
 
 template <int SB, int THREADS>
-int launch_leaf(Launcher &ln, const uint8_t *in, uint32_t level) {
+int launch_leaf(Launcher &ln, const uint8_t *in, bool in_padded, uint32_t level) {
   wt_tree *t = ln.t;
   LeafArgs a;
   a.in = in;
+  a.in_padded = in_padded ? 1 : 0;
   a.n = (uint32_t)t->n;
   a.L = t->L;
   a.NT = (uint32_t)t->NT;
@@ -797,10 +985,14 @@ int launch_leaf(Launcher &ln, const uint8_t *in, uint32_t level) {
   a.out = ln.out(level);
   a.cnt = ln.counts(level);
   a.ticket = ln.ticket();
+  a.spin_limit = ln.spin();
+  a.err = ln.err();
   auto kern = k_leaf<SB, THREADS>;
-  const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, 0, t->sms, t->cfg.ctas_per_sm));
+  constexpr size_t sm = leaf_smem_bytes<SB, THREADS>();
+  if (int rc = set_smem(kern, sm)) return rc;
+  const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
   ln.before(kLeaf);
-  kern<<<std::max(grid, 1), THREADS, 0, ln.st>>>(a);
+  kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
   ln.after();
   ++ln.pass;
   WT_CUDA(cudaGetLastError());
@@ -830,11 +1022,7 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.err = ln.err();
   auto kern = k_split<SB, THREADS>;
   constexpr uint32_t sm = split_smem_bytes<SB, THREADS>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    WT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr_set = true;
-  }
+  if (int rc = set_smem(kern, sm)) return rc;
   const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
   ln.before(kSplit);
   kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
@@ -882,7 +1070,7 @@ template <int SB, int THREADS>
 int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
   Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
   int rc;
-  if ((rc = launch_prepass<SB, THREADS>(ln, seq))) return rc;
+  if ((rc = launch_prepass<SB, THREADS>(ln, seq, seq_padded))) return rc;
   if ((rc = launch_tables(ln))) return rc;
   if (t->L == 0) return WT_OK;
   const uint8_t *in = seq;
@@ -893,7 +1081,7 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
     in = out;
     padded = true;
   }
-  return launch_leaf<SB, THREADS>(ln, in, t->L - 1);
+  return launch_leaf<SB, THREADS>(ln, in, padded, t->L - 1);
 }
 
 template <int SB>
@@ -1025,7 +1213,9 @@ int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
     }
     WT_CUDA(cudaMemcpyAsync(dst, seq, t->n * t->sb, cudaMemcpyDeviceToDevice, st));
     seq = static_cast<const uint8_t *>(dst);
+    padded = true;  // scratch buffers hold whole tiles
   }
+  if (seq == t->d_in_host) padded = true;
   if (t->n == 0) {
     // nothing to scan: zero bits/directories are already in place; node
     // starts are all zero
