@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
     uint32_t u[8 * SB];
     load_from_smem<SB, THREADS>(sIn, my0, u);
     const uint32_t word = a.L ? pack_bits<SB>(u, a.L - 1) & valid_mask(my0, nv) : 0u;
-    if (my0 + 32 <= nv) {
+    if (__all_sync(0xFFFFFFFFu, my0 + 32 <= nv)) {  // warp-uniform: the loop uses warp collectives
 #pragma unroll 8
       for (int q = 0; q < 32; ++q) {
         const uint32_t s = symbol_at<SB>(u, q);
