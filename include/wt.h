@@ -187,6 +187,33 @@ int wt_free(wt_tree *tree);
 /* Number of kernels one wt_rebuild of this tree launches. */
 int wt_kernels_per_build(const wt_tree *tree);
 
+/*
+ * Allocation-free build.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run --
+ * code inside a CUDA graph capture whose mode forbids allocation, hosts whose
+ * device allocator belongs to another runtime, and loops with a fixed memory
+ * footprint.  It builds the same outputs as wt_build (identical bits) but
+ * allocates nothing: the caller passes the input and every output, laid out
+ * as in wt_info_t (d_bits L*W uint32, d_rank L*(NB+1) uint64, d_zeros L
+ * uint64, d_node_start 2^L+1 uint64), and all scratch comes from one
+ * file-scope device array of 5 MiB that every GPU loading this library keeps
+ * until the process exits.
+ *   Limits: n * symbol_bytes <= 2^21 bytes and sigma <= 2^16; larger
+ *   problems return WT_ERR_ARG.
+ *   d_status (may be NULL) receives, in stream order, the device-detected
+ *   status of the build (0, WT_ERR_SYMBOL or WT_ERR_TIMEOUT).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls share the scratch array: calls whose work overlaps on the GPU
+ *   (different streams, or different host threads) race and corrupt each
+ *   other.  Serialise them on one stream.
+ * Errors: WT_ERR_ARG, WT_ERR_CUDA.
+ */
+int wt_build_noalloc(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                     uint32_t *d_bits, uint64_t *d_rank, uint64_t *d_zeros,
+                     uint64_t *d_node_start, int32_t *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

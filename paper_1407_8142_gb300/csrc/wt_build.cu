@@ -1335,3 +1335,153 @@ int wt_free(wt_tree *t) {
 }
 
 }  // extern "C"
+
+// ============================================================ allocation-free build
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+// being captured with a capture mode that forbids allocation, hosts whose
+// allocator is owned by another runtime or pinned at start-up, and real-time
+// loops that must not enter the driver's allocator.  wt_build_noalloc serves
+// them: the caller passes the input and every output buffer, and all scratch
+// the build needs (ping-pong symbol buffers, histogram, tile counts, node
+// tables, look-back state) is carved from one file-scope device array of
+// fixed size.  Every GPU that loads this library holds that array until the
+// process exits.
+#include <atomic>
+#include <mutex>
+
+namespace {
+
+constexpr uint64_t kStaticMaxSymbolBytes = 1ull << 21;  // n * symbol_bytes
+constexpr uint32_t kStaticMaxLevels = 16;               // sigma <= 65536
+constexpr size_t kStaticScratchBytes = 5ull << 20;      // 5 MiB
+constexpr int kStaticMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+unsigned char *g_static_ptr[kStaticMaxDevices] = {};
+std::atomic<uint32_t> g_static_builds{0};
+
+// Device address of g_static_scratch for the current device.  The name of
+// the array in host code is only a host-side stand-in; the device address is
+// looked up once per device, with that device current.
+int static_scratch(unsigned char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+    (void)cudaGetLastError();
+    return WT_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return WT_ERR_CUDA;
+    }
+    g_static_ptr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_static_ptr[dev];
+  return WT_OK;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int wt_build_noalloc(const void *d_seq, uint64_t n, uint32_t sigma,
+                                uint32_t symbol_bytes, uint32_t *d_bits, uint64_t *d_rank,
+                                uint64_t *d_zeros, uint64_t *d_node_start, int32_t *d_status,
+                                void *stream) {
+  if (!(symbol_bytes == 1 || symbol_bytes == 2 || symbol_bytes == 4)) return WT_ERR_ARG;
+  if (sigma == 0 || (uint64_t)sigma > (1ull << (8 * symbol_bytes))) return WT_ERR_ARG;
+  if (n * symbol_bytes > kStaticMaxSymbolBytes) return WT_ERR_ARG;
+  const uint32_t L = levels_of(sigma);
+  if (L > kStaticMaxLevels) return WT_ERR_ARG;
+  if (n && !d_seq) return WT_ERR_ARG;
+  if (!d_node_start || (L && (!d_bits || !d_rank || !d_zeros))) return WT_ERR_ARG;
+
+  unsigned char *base = nullptr;
+  if (int rc = static_scratch(&base)) return rc;
+
+  wt_tree t;  // on the stack: describes the build, owns nothing
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&t.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return WT_ERR_CUDA;
+  }
+  t.n = n;
+  t.sigma = sigma;
+  t.sb = symbol_bytes;
+  t.L = L;
+  t.NB = (n + 511) / 512;
+  t.W = 16 * t.NB;
+  t.threads = pick_threads(n, symbol_bytes, t.sms, 0);
+  t.T = 32ull * t.threads;
+  t.NT = std::max<uint64_t>(1, (n + t.T - 1) / t.T);
+  t.d_bits = d_bits;
+  t.d_rank = reinterpret_cast<unsigned long long *>(d_rank);
+  t.d_zeros = reinterpret_cast<unsigned long long *>(d_zeros);
+  t.d_node_start = reinterpret_cast<unsigned long long *>(d_node_start);
+
+  // carve the scratch
+  const uint64_t nbins = 1ull << L;
+  const uint32_t Lz = std::max<uint32_t>(L, 1);
+  t.counts_per_level = t.NT + (t.NT >> 6) + 1 + (t.NT >> 12) + 1;
+  t.ctrl_words = kCtrlWords + nbins + (uint64_t)Lz * t.counts_per_level;
+  t.status_n = std::max<uint64_t>({t.NT, (uint64_t)hist_blocks(L), (uint64_t)tables_blocks(L), 1});
+  t.buf_bytes = t.NT * t.T * symbol_bytes + 16;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char *p = base + off;
+    off += round256(bytes);
+    return p;
+  };
+  t.d_buf[0] = take(t.buf_bytes);
+  t.d_buf[1] = take(t.buf_bytes);
+  t.d_tab = reinterpret_cast<uint2 *>(take(std::max<uint64_t>(1, nbins / 2) * sizeof(uint2)));
+  t.d_ctrl = reinterpret_cast<uint32_t *>(take(t.ctrl_words * 4));
+  t.d_hist = t.d_ctrl + kCtrlWords;
+  t.d_counts = t.d_hist + nbins;
+  t.d_status = reinterpret_cast<unsigned long long *>(take(t.status_n * 8));
+  if (off > kStaticScratchBytes) return WT_ERR_ARG;
+  // the look-back state is never cleared: every build tags it with a new epoch
+  t.build_count = g_static_builds.fetch_add(1) + 1;
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // tickets, error word, histogram and tile counts must start at zero
+  WT_CUDA(cudaMemsetAsync(t.d_ctrl, 0, t.ctrl_words * 4, st));
+  if (n == 0) {
+    if (L) {
+      WT_CUDA(cudaMemsetAsync(d_rank, 0, (size_t)L * 8, st));
+      WT_CUDA(cudaMemsetAsync(d_zeros, 0, (size_t)L * 8, st));
+    }
+    WT_CUDA(cudaMemsetAsync(d_node_start, 0, (nbins + 1) * 8, st));
+    if (d_status) WT_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
+    return WT_OK;
+  }
+  const uint8_t *seq = static_cast<const uint8_t *>(d_seq);
+  bool padded = false;
+  if (reinterpret_cast<uintptr_t>(seq) & 15u) {
+    // stage an unaligned input in the buffer the first pass does not write
+    void *dst = L >= 2 ? t.d_buf[1] : t.d_buf[0];
+    WT_CUDA(cudaMemcpyAsync(dst, seq, n * symbol_bytes, cudaMemcpyDeviceToDevice, st));
+    seq = static_cast<const uint8_t *>(dst);
+    padded = true;
+  }
+  int rc = WT_ERR_ARG;
+  switch (symbol_bytes) {
+    case 1: rc = run_build_sb<1>(&t, seq, padded, st); break;
+    case 2: rc = run_build_sb<2>(&t, seq, padded, st); break;
+    case 4: rc = run_build_sb<4>(&t, seq, padded, st); break;
+  }
+  if (rc == WT_OK && d_status)
+    WT_CUDA(cudaMemcpyAsync(d_status, t.d_ctrl + kCtrlErr, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return rc;
+}
+

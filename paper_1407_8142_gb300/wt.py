@@ -72,6 +72,7 @@ SIGNATURES = {
     "wt_profile_read": (ctypes.c_int, [P, P, P, I32]),
     "wt_free": (ctypes.c_int, [P]),
     "wt_kernels_per_build": (ctypes.c_int, [P]),
+    "wt_build_noalloc": (ctypes.c_int, [P, U64, U32, U32, P, P, P, P, P, P]),
 }
 
 
