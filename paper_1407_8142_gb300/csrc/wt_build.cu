@@ -436,96 +436,55 @@ __device__ __forceinline__ uint32_t count_bit(uint32_t w, uint32_t k1) {
   return (w >> k1) & 1u;
 }
 
-// Copy one run of `len` symbols, staged in shared memory at byte offset soff
-// of a 16-byte aligned word array, to global symbol position gpos; executed
-// by one warp.  Unaligned head and tail bytes are stored singly, the body as
-// aligned 16-byte stores assembled from aligned 16-byte shared loads (the next
-// lane's block supplies the overhang).  Bit k1 of the copied symbols is
-// counted into cnt_a (destination tile of position split_at - 1 or earlier)
-// and cnt_b (positions >= split_at).  Writes past n are dropped (reachable
-// only after a device error).
+// Copy one run of `len` bytes staged in shared memory at byte offset soff of
+// `stage` to global byte offset g of `gout`; executed by one warp.  The run
+// was staged so that soff = g (mod 16): every full 16-byte chunk is one
+// aligned shared load and one aligned global store; the unaligned head and
+// tail bytes are copied singly.  Bit k1 of the copied symbols is counted into
+// cnt_a (symbol positions before split_at) and cnt_b (from split_at on).
+// Writes past gend (n * SB) are dropped (reachable only after a device error).
 template <int SB>
-__device__ __forceinline__ void warp_copy_run(const uint32_t *sbase, uint32_t soff, uint8_t *gout,
-                                              uint64_t gpos, uint32_t len, uint32_t n,
-                                              uint64_t split_at, uint32_t k1, uint32_t &cnt_a,
-                                              uint32_t &cnt_b) {
-  if (gpos >= n) return;
-  if (gpos + len > n) len = (uint32_t)(n - gpos);
-  if (len == 0) return;
-  uint8_t *dst = gout + gpos * SB;
-  const uint32_t bytes = len * SB;
-  const uint8_t *sb = reinterpret_cast<const uint8_t *>(sbase);
-  const uint32_t mis = (uint32_t)(reinterpret_cast<uintptr_t>(dst) & 15u);
-  const uint32_t head = min(bytes, (16u - mis) & 15u);
-  const uint32_t nch = (bytes - head) >> 4;
-  const uint32_t tail0 = head + (nch << 4);
-  const uint32_t tail = bytes - tail0;
+__device__ __forceinline__ void warp_copy_run(const uint8_t *stage, uint32_t soff, uint8_t *gout,
+                                              uint64_t g, uint32_t len, uint64_t gend,
+                                              uint32_t split_at, uint32_t mk1, uint32_t k1,
+                                              uint32_t &cnt_a, uint32_t &cnt_b) {
+  if (g >= gend) return;
+  if (g + len > gend) len = (uint32_t)(gend - g);
   const uint32_t lane = threadIdx.x & 31;
-  if (lane < head + tail) {
+  const uint32_t head = min(len, (16u - ((uint32_t)g & 15u)) & 15u);
+  const uint32_t nch = (len - head) >> 4;
+  const uint32_t tail0 = head + (nch << 4);
+  const uint32_t nb = head + (len - tail0);  // single bytes: head, then tail
+  const uint32_t p0 = (uint32_t)(g / SB);    // symbol position of the run's first byte
+  if (lane < nb) {
     const uint32_t o = lane < head ? lane : tail0 + (lane - head);
-    dst[o] = sb[soff + o];
+    gout[g + o] = stage[soff + o];
     if (o % SB == 0) {  // first byte of a symbol: count it
-      uint32_t s;
-      if (SB == 1) s = sb[soff + o];
-      else if (SB == 2) s = *reinterpret_cast<const uint16_t *>(sb + soff + o);
-      else s = *reinterpret_cast<const uint32_t *>(sb + soff + o);
-      const uint32_t one = (s >> k1) & 1u;
-      if (gpos + o / SB >= split_at) cnt_b += one;
+      uint32_t v;
+      if (SB == 1) v = stage[soff + o];
+      else if (SB == 2) v = *reinterpret_cast<const uint16_t *>(stage + soff + o);
+      else v = *reinterpret_cast<const uint32_t *>(stage + soff + o);
+      const uint32_t one = (v >> k1) & 1u;
+      if (p0 + o / SB >= split_at) cnt_b += one;
       else cnt_a += one;
     }
   }
-  const uint32_t a0 = soff + head;       // shared byte offset of chunk 0
-  const uint32_t aw = (a0 & ~15u) >> 2;  // its aligned 16-byte block, in words
-  const uint32_t sh = a0 & 15u;          // byte offset inside that block (run-uniform)
-  const uint32_t r = (sh & 3u) * 8u;
-  for (uint32_t cb = 0; cb < nch; cb += 32) {
-    const uint32_t c = cb + lane;
-    const bool active = c < nch;
-    uint4 cur = make_uint4(0, 0, 0, 0), v;
-    // block c <= nch: the block after the last chunk supplies its overhang
-    if (c <= nch) cur = *reinterpret_cast<const uint4 *>(sbase + aw + 4 * c);
-    if (sh == 0) {
-      v = cur;
-    } else {
-      uint4 nx;
-      nx.x = __shfl_down_sync(0xFFFFFFFFu, cur.x, 1);
-      nx.y = __shfl_down_sync(0xFFFFFFFFu, cur.y, 1);
-      nx.z = __shfl_down_sync(0xFFFFFFFFu, cur.z, 1);
-      nx.w = __shfl_down_sync(0xFFFFFFFFu, cur.w, 1);
-      if (lane == 31 && active) nx = *reinterpret_cast<const uint4 *>(sbase + aw + 4 * (c + 1));
-      switch (sh >> 2) {  // words [sh/4, sh/4 + 5) of cur||nx, shifted by r bits
-        case 0:
-          v = make_uint4(__funnelshift_r(cur.x, cur.y, r), __funnelshift_r(cur.y, cur.z, r),
-                         __funnelshift_r(cur.z, cur.w, r), __funnelshift_r(cur.w, nx.x, r));
-          break;
-        case 1:
-          v = make_uint4(__funnelshift_r(cur.y, cur.z, r), __funnelshift_r(cur.z, cur.w, r),
-                         __funnelshift_r(cur.w, nx.x, r), __funnelshift_r(nx.x, nx.y, r));
-          break;
-        case 2:
-          v = make_uint4(__funnelshift_r(cur.z, cur.w, r), __funnelshift_r(cur.w, nx.x, r),
-                         __funnelshift_r(nx.x, nx.y, r), __funnelshift_r(nx.y, nx.z, r));
-          break;
-        default:
-          v = make_uint4(__funnelshift_r(cur.w, nx.x, r), __funnelshift_r(nx.x, nx.y, r),
-                         __funnelshift_r(nx.y, nx.z, r), __funnelshift_r(nx.z, nx.w, r));
-          break;
-      }
-    }
-    if (active) {
-      const uint32_t o = head + (c << 4);
-      *reinterpret_cast<uint4 *>(dst + o) = v;
-      const uint32_t ones = count_bit<SB>(v.x, k1) + count_bit<SB>(v.y, k1) +
-                            count_bit<SB>(v.z, k1) + count_bit<SB>(v.w, k1);
-      if (gpos + o / SB >= split_at) cnt_b += ones;
-      else cnt_a += ones;
-    }
+  const uint4 *src = reinterpret_cast<const uint4 *>(stage + soff + head);
+  uint4 *dst = reinterpret_cast<uint4 *>(gout + g + head);
+  const uint32_t pc0 = p0 + head / SB;  // symbol position of chunk 0
+  for (uint32_t c = lane; c < nch; c += 32) {
+    const uint4 v = src[c];
+    dst[c] = v;
+    const uint32_t ones = __popc(v.x & mk1) + __popc(v.y & mk1) + __popc(v.z & mk1) + __popc(v.w & mk1);
+    if (pc0 + c * (16 / SB) >= split_at) cnt_b += ones;
+    else cnt_a += ones;
   }
 }
 
-// per-warp staging: 1024 symbols plus 32 bytes for the shifted reads
+// per-warp staging: 1024 symbols plus room to align both runs to their
+// global 16-byte phase
 template <int SB>
-__host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * SB + 32u; }
+__host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * SB + 48u; }
 
 constexpr uint32_t kTabSmem = 1024;  // level tables up to this many nodes live in shared memory
 
@@ -556,7 +515,7 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
   pipe.bar = reinterpret_cast<uint64_t *>(sTab + kTabSmem);
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
   uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
-  unsigned long long *const sRun = reinterpret_cast<unsigned long long *>(sCnt + 4);  // 2 run starts
+  uint32_t *const sRun = sCnt + 4;                   // 2 run starts
   pipe.in = a.in;
   pipe.in_padded = a.in_padded;
   pipe.n = a.n;
@@ -627,9 +586,12 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + pw, total);
 
     // Pass B: stable split of the warp's segment into its staging area,
-    // zeros first.  In step s lane i holds the G symbols at 32*G*s + G*i:
-    // one 32-bit shared load; their bits come from the bitmap word, the ones
-    // before them from the word prefix plus a popcount.
+    // zeros first.  In step s lane i holds the G symbols at 32*G*s + G*i
+    // (one 64-bit shared load); their bits come from the bitmap word, the
+    // ones before them from the word prefix plus a popcount.  In a tile that
+    // lies in one node, each run is staged at the 16-byte phase of its
+    // destination in T_{l+1}, so that it is written with aligned 16-byte
+    // copies.
     const uint32_t seg = 1024 * warp;
     const uint32_t nvw = nv > seg ? min(nv - seg, 1024u) : 0u;  // symbols of this warp
     const uint32_t tw = __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -638,42 +600,57 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
     const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
     const uint32_t Zb = (uint32_t)start - R;  // zeros of level l before the tile
+    const uint32_t Zw = Zb + seg - Pw;        // zeros of level l before the warp
+    const uint32_t Ow = R + Pw;               // ones of level l before the warp
+    const bool one_node = pf == pl;
+    uint32_t gz = 0, go = 0, zoff = 0, ooff = nzw * SB;  // destinations, staging offsets (bytes)
+    if (one_node) {
+      const uint2 tb = tab[pf];
+      gz = tb.x + Zw;
+      go = tb.y + Ow;
+      zoff = (gz * SB) & 15u;
+      ooff = ((zoff + nzw * SB + 15u) & ~15u) + ((go * SB) & 15u);
+    }
     if (nvw) {
-      const uint32_t wsub = lane / LPW;
-      const uint32_t bo = (lane % LPW) * G;
+      constexpr uint32_t G8 = 8 / SB;     // symbols per lane per step
+      constexpr uint32_t LPW8 = 32 / G8;  // lanes per bitmap word
+      const uint32_t wsub = lane / LPW8;
+      const uint32_t bo = (lane % LPW8) * G8;
       const uint32_t lowmask = (1u << bo) - 1u;
       const uint8_t *segIn = sIn + seg * SB;
+      Sym *const zS = reinterpret_cast<Sym *>(stage + zoff);
+      Sym *const oS = reinterpret_cast<Sym *>(stage + ooff);
       if (nvw == 1024) {
-#pragma unroll 4
-        for (uint32_t s = 0; s < 32 / G; ++s) {
-          const uint32_t pos0 = 32 * G * s + G * lane;
-          const uint2 wp = sWP[32 * warp + G * s + wsub];
-          const uint32_t grp = *reinterpret_cast<const uint32_t *>(segIn + pos0 * SB);
+#pragma unroll 2
+        for (uint32_t s = 0; s < 32 / G8; ++s) {
+          const uint32_t pos0 = 32 * G8 * s + G8 * lane;
+          const uint2 wp = sWP[32 * warp + G8 * s + wsub];
+          const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
           const uint32_t bits = wp.x >> bo;
           const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the warp
-          uint32_t o = nzw + Rl, z = pos0 - Rl;
+          uint32_t o = Rl, z = pos0 - Rl;
 #pragma unroll
-          for (uint32_t j = 0; j < G; ++j) {
-            const uint32_t b = (bits >> j) & 1u;
-            stageS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
-            o += b;
-            z += b ^ 1u;
+          for (uint32_t j = 0; j < G8; ++j) {
+            const uint32_t w = j < G8 / 2 ? grp.x : grp.y;
+            const Sym v = (Sym)(w >> (8 * SB * (j % (G8 / 2))));
+            if ((bits >> j) & 1u) oS[o++] = v;
+            else zS[z++] = v;
           }
         }
       } else {
-        for (uint32_t s = 0; s < 32 / G; ++s) {
-          const uint32_t pos0 = 32 * G * s + G * lane;
-          const uint2 wp = sWP[32 * warp + G * s + wsub];
-          const uint32_t grp = *reinterpret_cast<const uint32_t *>(segIn + pos0 * SB);
+        for (uint32_t s = 0; s < 32 / G8; ++s) {
+          const uint32_t pos0 = 32 * G8 * s + G8 * lane;
+          const uint2 wp = sWP[32 * warp + G8 * s + wsub];
+          const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
           const uint32_t bits = wp.x >> bo;
           const uint32_t Rl = wp.y + __popc(wp.x & lowmask);
-          uint32_t o = nzw + Rl, z = pos0 - Rl;
-          for (uint32_t j = 0; j < G; ++j) {
+          uint32_t o = Rl, z = pos0 - Rl;
+          for (uint32_t j = 0; j < G8; ++j) {
             if (pos0 + j < nvw) {
-              const uint32_t b = (bits >> j) & 1u;
-              stageS[b ? o : z] = (Sym)(grp >> (8 * SB * j));
-              o += b;
-              z += b ^ 1u;
+              const uint32_t w = j < G8 / 2 ? grp.x : grp.y;
+              const Sym v = (Sym)(w >> (8 * SB * (j % (G8 / 2))));
+              if ((bits >> j) & 1u) oS[o++] = v;
+              else zS[z++] = v;
             }
           }
         }
@@ -682,18 +659,16 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
 
       // Phase 2: the warp writes its zeros and ones to T_{l+1}, counting the
       // next level's ones per destination tile.
-      const uint32_t Zw = Zb + seg - Pw;  // zeros of level l before the warp
-      const uint32_t Ow = R + Pw;         // ones of level l before the warp
-      if (pf == pl) {
+      if (one_node) {
         // the whole tile lies in one node: its zeros and ones are two runs
         const uint2 tb = tab[pf];
-        const uint32_t *sO = reinterpret_cast<const uint32_t *>(stage);
-        const uint64_t r0 = (uint64_t)tb.x + Zb;  // run starts
-        const uint64_t r1 = (uint64_t)tb.y + R;
-        const uint64_t s0 = ((r0 >> a.log2T) + 1) << a.log2T, s1 = ((r1 >> a.log2T) + 1) << a.log2T;
+        const uint32_t r0 = tb.x + Zb, r1 = tb.y + R;  // where the tile's runs start
+        const uint32_t s0 = ((r0 >> a.log2T) + 1) << a.log2T, s1 = ((r1 >> a.log2T) + 1) << a.log2T;
+        const uint32_t mk1 = (SB == 1 ? 0x01010101u : SB == 2 ? 0x00010001u : 1u) << k1;
+        const uint64_t gend = (uint64_t)a.n * SB;
         uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
-        warp_copy_run<SB>(sO, 0, a.out, (uint64_t)tb.x + Zw, nzw, a.n, s0, k1, c0a, c0b);
-        warp_copy_run<SB>(sO, nzw * SB, a.out, (uint64_t)tb.y + Ow, tw, a.n, s1, k1, c1a, c1b);
+        warp_copy_run<SB>(stage, zoff, a.out, (uint64_t)gz * SB, nzw * SB, gend, s0, mk1, k1, c0a, c0b);
+        warp_copy_run<SB>(stage, ooff, a.out, (uint64_t)go * SB, tw * SB, gend, s1, mk1, k1, c1a, c1b);
         const uint32_t v0 = __reduce_add_sync(0xFFFFFFFFu, c0a);
         const uint32_t v1 = __reduce_add_sync(0xFFFFFFFFu, c0b);
         const uint32_t v2 = __reduce_add_sync(0xFFFFFFFFu, c1a);
@@ -735,13 +710,13 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
     pre = pre_next;
     __syncthreads();
-    if (tid < 4 && pf == pl) {
+    if (tid < 4 && one_node) {
       // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
       const uint32_t v = sCnt[tid];
       if (v) {
         sCnt[tid] = 0;
-        const uint64_t dt = (sRun[tid >> 1] >> a.log2T) + (tid & 1);
-        if (dt < a.NT) counts_add(a.cout, (uint32_t)dt, v);
+        const uint32_t dt = (sRun[tid >> 1] >> a.log2T) + (tid & 1);
+        if (dt < a.NT) counts_add(a.cout, dt, v);
       }
     }
   }
