@@ -481,6 +481,38 @@ __device__ __forceinline__ void warp_copy_run(const uint8_t *stage, uint32_t sof
   }
 }
 
+
+// Store v (the low SB bytes) at shared address oa if bit != 0, else at za,
+// and advance that address by one symbol.  Predicated, branch-free.
+template <int SB>
+__device__ __forceinline__ void scatter_one(uint32_t bit, uint32_t &oa, uint32_t &za, uint32_t v) {
+  if (SB == 1) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u8 [%0], %3;\n\t@!p st.shared.u8 [%1], %3;\n\t"
+        "@p add.u32 %0, %0, 1;\n\t@!p add.u32 %1, %1, 1;\n\t}"
+        : "+r"(oa), "+r"(za)
+        : "r"(bit), "r"(v)
+        : "memory");
+  } else if (SB == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u16 [%0], %3;\n\t@!p st.shared.u16 [%1], %3;\n\t"
+        "@p add.u32 %0, %0, 2;\n\t@!p add.u32 %1, %1, 2;\n\t}"
+        : "+r"(oa), "+r"(za)
+        : "r"(bit), "h"((unsigned short)v)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u32 [%0], %3;\n\t@!p st.shared.u32 [%1], %3;\n\t"
+        "@p add.u32 %0, %0, 4;\n\t@!p add.u32 %1, %1, 4;\n\t}"
+        : "+r"(oa), "+r"(za)
+        : "r"(bit), "r"(v)
+        : "memory");
+  }
+}
+
 // per-warp staging: 1024 symbols plus room to align both runs to their
 // global 16-byte phase
 template <int SB>
@@ -498,7 +530,7 @@ constexpr uint32_t split_smem_bytes() {
 }
 
 template <int SB, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 512 ? 3 : 1) k_split(SplitArgs a) {
+__global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t NW = THREADS / 32;
@@ -516,7 +548,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == 512 ? 3 : 1) k_split(Split
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
   uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
   uint32_t *const sRun = sCnt + 4;                   // 2 run starts
-  uint32_t *const sSel = sRun + 2;                   // 16 byte-permute selectors
   pipe.in = a.in;
   pipe.in_padded = a.in_padded;
   pipe.n = a.n;
@@ -537,17 +568,6 @@ __global__ void __launch_bounds__(THREADS, THREADS == 512 ? 3 : 1) k_split(Split
   if (tab_smem)
     for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
   if (tid < 4) sCnt[tid] = 0;
-  if (tid < 16) {
-    // selector that gathers the bytes j of a word with bit j of tid set to
-    // the low end, in order; unused result bytes take byte 4 (zero)
-    uint32_t sel = 0x4444u, k = 0;
-    for (uint32_t j = 0; j < 4; ++j)
-      if ((tid >> j) & 1u) {
-        sel = (sel & ~(0xFu << (4 * k))) | (j << (4 * k));
-        ++k;
-      }
-    sSel[tid] = sel;
-  }
   if (tid == 0) pipe.prologue();
   __syncthreads();
   PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
@@ -632,52 +652,11 @@ __global__ void __launch_bounds__(THREADS, THREADS == 512 ? 3 : 1) k_split(Split
       const uint8_t *segIn = sIn + seg * SB;
       Sym *const zS = reinterpret_cast<Sym *>(stage + zoff);
       Sym *const oS = reinterpret_cast<Sym *>(stage + ooff);
-      if (SB == 1) {
-        // One-byte symbols: per lane and step, 8 symbols (two words).  Each
-        // word's zero bytes and one bytes are packed by one byte-permute each
-        // (selector by the word's 4 bits), the two words' pieces are joined in
-        // a 64-bit register, and each piece is OR-ed into the zeroed staging
-        // area (at most three 32-bit words, shared with the neighbouring
-        // lanes' pieces only at its ends).
-        uint32_t *const stw = reinterpret_cast<uint32_t *>(stage);
-        for (uint32_t i = lane; i < stage_bytes<SB>() / 16; i += 32)
-          reinterpret_cast<uint4 *>(stage)[i] = make_uint4(0, 0, 0, 0);
-        __syncwarp();
-        for (uint32_t s = 0; s < 32 / G8; ++s) {
-          const uint32_t pos0 = 32 * G8 * s + G8 * lane;
-          const uint2 wp = sWP[32 * warp + G8 * s + wsub];
-          const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
-          const uint32_t vm = pos0 < nvw ? (nvw - pos0 >= 8 ? 0xFFu : (1u << (nvw - pos0)) - 1u) : 0u;
-          const uint32_t bits = (wp.x >> bo) & vm;     // 1 = goes to the ones
-          const uint32_t zbits = ~(wp.x >> bo) & vm;   // 1 = goes to the zeros
-          const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the warp
-          const uint32_t sel0 = sSel[bits & 15u], sel1 = sSel[(bits >> 4) & 15u];
-          const uint32_t zsel0 = sSel[zbits & 15u], zsel1 = sSel[(zbits >> 4) & 15u];
-          const uint32_t n1a = __popc(bits & 15u), n0a = __popc(zbits & 15u);
-          // packed pieces (unused bytes are zero)
-          const unsigned long long o64 = ((unsigned long long)__byte_perm(grp.y, 0, sel1) << (8 * n1a)) |
-                                         __byte_perm(grp.x, 0, sel0);
-          const unsigned long long z64 = ((unsigned long long)__byte_perm(grp.y, 0, zsel1) << (8 * n0a)) |
-                                         __byte_perm(grp.x, 0, zsel0);
-          const uint32_t zp = zoff + pos0 - Rl, op = ooff + Rl;  // byte offsets in the staging
-          {
-            const uint32_t sh = (zp & 3u) * 8u, w = zp >> 2;
-            const uint32_t lo = (uint32_t)z64, hi = (uint32_t)(z64 >> 32);
-            const uint32_t x0 = lo << sh, x1 = __funnelshift_l(lo, hi, sh), x2 = __funnelshift_l(hi, 0u, sh);
-            if (x0) atomicOr(&stw[w], x0);
-            if (x1) atomicOr(&stw[w + 1], x1);
-            if (x2) atomicOr(&stw[w + 2], x2);
-          }
-          {
-            const uint32_t sh = (op & 3u) * 8u, w = op >> 2;
-            const uint32_t lo = (uint32_t)o64, hi = (uint32_t)(o64 >> 32);
-            const uint32_t x0 = lo << sh, x1 = __funnelshift_l(lo, hi, sh), x2 = __funnelshift_l(hi, 0u, sh);
-            if (x0) atomicOr(&stw[w], x0);
-            if (x1) atomicOr(&stw[w + 1], x1);
-            if (x2) atomicOr(&stw[w + 2], x2);
-          }
-        }
-      } else if (nvw == 1024) {
+      if (nvw == 1024) {
+        // Each symbol goes to the running zero or one pointer of its lane:
+        // one predicate, two predicated stores, two predicated increments --
+        // no branch, whatever the bits.
+        const uint32_t zbase = smem_addr(zS), obase = smem_addr(oS);
 #pragma unroll 2
         for (uint32_t s = 0; s < 32 / G8; ++s) {
           const uint32_t pos0 = 32 * G8 * s + G8 * lane;
@@ -685,16 +664,12 @@ __global__ void __launch_bounds__(THREADS, THREADS == 512 ? 3 : 1) k_split(Split
           const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
           const uint32_t bits = wp.x >> bo;
           const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the warp
-          uint32_t o = Rl, z = pos0 - Rl;
+          uint32_t oa = obase + Rl * SB, za = zbase + (pos0 - Rl) * SB;
 #pragma unroll
           for (uint32_t j = 0; j < G8; ++j) {
             const uint32_t w = j < G8 / 2 ? grp.x : grp.y;
-            const Sym v = (Sym)(w >> (8 * SB * (j % (G8 / 2))));
-            const uint32_t b = (bits >> j) & 1u;
-            Sym *const dst = b ? oS + o : zS + z;
-            *dst = v;
-            o += b;
-            z += b ^ 1u;
+            const uint32_t v = w >> (8 * SB * (j % (G8 / 2)));
+            scatter_one<SB>(bits & (1u << j), oa, za, v);
           }
         }
       } else {
