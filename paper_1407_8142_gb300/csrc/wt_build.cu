@@ -483,30 +483,29 @@ __device__ __forceinline__ void warp_copy_run(const uint8_t *stage, uint32_t sof
 
 
 // Store v (the low SB bytes) at shared address oa if bit != 0, else at za,
-// and advance that address by one symbol: one select, one store, two
-// predicated increments -- branch-free.
+// and advance that address by one symbol.  Predicated, branch-free.
 template <int SB>
 __device__ __forceinline__ void scatter_one(uint32_t bit, uint32_t &oa, uint32_t &za, uint32_t v) {
   if (SB == 1) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .u32 a;\n\tsetp.ne.u32 p, %2, 0;\n\t"
-        "selp.u32 a, %0, %1, p;\n\tst.shared.u8 [a], %3;\n\t"
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u8 [%0], %3;\n\t@!p st.shared.u8 [%1], %3;\n\t"
         "@p add.u32 %0, %0, 1;\n\t@!p add.u32 %1, %1, 1;\n\t}"
         : "+r"(oa), "+r"(za)
         : "r"(bit), "r"(v)
         : "memory");
   } else if (SB == 2) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .u32 a;\n\tsetp.ne.u32 p, %2, 0;\n\t"
-        "selp.u32 a, %0, %1, p;\n\tst.shared.u16 [a], %3;\n\t"
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u16 [%0], %3;\n\t@!p st.shared.u16 [%1], %3;\n\t"
         "@p add.u32 %0, %0, 2;\n\t@!p add.u32 %1, %1, 2;\n\t}"
         : "+r"(oa), "+r"(za)
         : "r"(bit), "h"((unsigned short)v)
         : "memory");
   } else {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .u32 a;\n\tsetp.ne.u32 p, %2, 0;\n\t"
-        "selp.u32 a, %0, %1, p;\n\tst.shared.u32 [a], %3;\n\t"
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u32 [%0], %3;\n\t@!p st.shared.u32 [%1], %3;\n\t"
         "@p add.u32 %0, %0, 4;\n\t@!p add.u32 %1, %1, 4;\n\t}"
         : "+r"(oa), "+r"(za)
         : "r"(bit), "r"(v)
