@@ -529,66 +529,41 @@ constexpr uint32_t split_smem_bytes() {
          8u * (THREADS / 32) + 8u * kTabSmem + 192u;
 }
 
+// Shared-memory working set of one split tile.
+struct SplitShared {
+  uint8_t *stage;  // per-warp staging areas
+  uint2 *wp;       // per thread {bit word, warp-local ones-prefix}
+  uint2 *wt;       // per warp {ones, prefix share}
+  uint32_t *cnt;   // 4 run counters
+  uint32_t *run;   // 2 run starts
+};
+
+// One tile of the split pass over level a.level: bits and directory of the
+// level, stable split into T_{level+1}, next-level ones per destination tile.
+// sIn holds the tile's symbols; share is this thread's part of the tile's
+// ones-prefix (summed over the block here).  Ends with a block barrier,
+// after which thread 0 has stored ring_value to *ring_slot (if non-null).
 template <int SB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
+__device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab, uint32_t tile,
+                                           const uint8_t *sIn, uint32_t share_part,
+                                           const SplitShared &sm, uint32_t *ring_slot,
+                                           uint32_t ring_value) {
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t NW = THREADS / 32;
-  constexpr uint32_t G = 4 / SB;        // symbols per lane per step of pass B
-  constexpr uint32_t LPW = 32 / G;      // lanes per bitmap word in pass B
-  extern __shared__ __align__(128) uint8_t smem[];
-  TilePipe<SB, THREADS> pipe;
-  pipe.sIn0 = smem;
-  pipe.sIn1 = smem + pipe.TB;
-  uint8_t *const sStage = smem + 2 * pipe.TB;
-  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());  // {word, prefix}
-  uint2 *const sWT = sWP + THREADS;                  // per warp {ones, prefix share}
-  uint2 *const sTab = sWT + NW;                      // level table (small levels)
-  pipe.bar = reinterpret_cast<uint64_t *>(sTab + kTabSmem);
-  pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
-  uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
-  uint32_t *const sRun = sCnt + 4;                   // 2 run starts
-  pipe.in = a.in;
-  pipe.in_padded = a.in_padded;
-  pipe.n = a.n;
-  pipe.NT = a.NT;
-  pipe.ticket = a.ticket;
-
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t k = a.L - 1 - a.level;   // bit of this level
   const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
   const uint32_t pshift = a.L - a.level;  // node prefix = symbol >> pshift
   const uint32_t lmask = (1u << a.L) - 1u;
-  const uint32_t nodes = 1u << a.level;
-  const bool tab_smem = nodes <= kTabSmem;
-  const uint2 *const tab = tab_smem ? sTab : a.tab;
-  uint8_t *const stage = sStage + warp * stage_bytes<SB>();
+  uint8_t *const stage = sm.stage + warp * stage_bytes<SB>();
   Sym *const stageS = reinterpret_cast<Sym *>(stage);
-
-  if (tab_smem)
-    for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
-  if (tid < 4) sCnt[tid] = 0;
-  if (tid == 0) pipe.prologue();
-  __syncthreads();
-  PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
-
-  for (uint32_t it = 0;; ++it) {
-    const uint32_t tile = pipe.ring[it % 3];
-    if (tile >= a.NT) break;
-    const uint32_t nxt = pipe.ring[(it + 1) % 3];
-    uint32_t nn = 0;
-    if (tid == 0) nn = pipe.advance(it, nxt);
-    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
-    const bool ok = pipe.wait(it, a.spin_limit, a.err);
-    if (__syncthreads_or(!ok)) {
-      pipe.drain(it, a.spin_limit, a.err);
-      __syncthreads();
-      break;
-    }
-    const uint64_t start = (uint64_t)tile * T;
-    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
-    uint8_t *const sIn = pipe.data(it);
-    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+  uint2 *const sWP = sm.wp;
+  uint2 *const sWT = sm.wt;
+  uint32_t *const sCnt = sm.cnt;
+  uint32_t *const sRun = sm.run;
+  const uint64_t start = (uint64_t)tile * T;
+  const uint32_t nv = (uint32_t)umin64(T, a.n - start);
 
     // Pass A: 32 consecutive symbols per thread -> one bitmap word; warp scan
     // of the ones.
@@ -608,7 +583,7 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
     }
     const uint32_t pw = incl - pc;  // ones before this word, within the warp
     sWP[tid] = make_uint2(word, pw);
-    const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, pre.sum());
+    const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, share_part);
     if (lane == 31) sWT[warp] = make_uint2(incl, share);
     __syncthreads();
     const uint2 wv = lane < NW ? sWT[lane] : make_uint2(0, 0);
@@ -745,18 +720,74 @@ __global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
         }
       }
     }
-    if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
-    pre = pre_next;
+    if (ring_slot) *ring_slot = ring_value;
     __syncthreads();
     if (tid < 4 && one_node) {
       // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
-      const uint32_t v = sCnt[tid];
+      const uint32_t v = sm.cnt[tid];
       if (v) {
-        sCnt[tid] = 0;
-        const uint32_t dt = (sRun[tid >> 1] >> a.log2T) + (tid & 1);
+        sm.cnt[tid] = 0;
+        const uint32_t dt = (sm.run[tid >> 1] >> a.log2T) + (tid & 1);
         if (dt < a.NT) counts_add(a.cout, dt, v);
       }
     }
+}
+
+template <int SB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t NW = THREADS / 32;
+  extern __shared__ __align__(128) uint8_t smem[];
+  TilePipe<SB, THREADS> pipe;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint8_t *const sStage = smem + 2 * pipe.TB;
+  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());  // {word, prefix}
+  uint2 *const sWT = sWP + THREADS;                  // per warp {ones, prefix share}
+  uint2 *const sTab = sWT + NW;                      // level table (small levels)
+  pipe.bar = reinterpret_cast<uint64_t *>(sTab + kTabSmem);
+  pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
+  uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
+  uint32_t *const sRun = sCnt + 4;                   // 2 run starts
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
+
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nodes = 1u << a.level;
+  const bool tab_smem = nodes <= kTabSmem;
+  const uint2 *const tab = tab_smem ? sTab : a.tab;
+
+  if (tab_smem)
+    for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
+  if (tid < 4) sCnt[tid] = 0;
+  if (tid == 0) pipe.prologue();
+  __syncthreads();
+  PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
+
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = pipe.ring[it % 3];
+    if (tile >= a.NT) break;
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = pipe.advance(it, nxt);
+    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
+    if (__syncthreads_or(!ok)) {
+      pipe.drain(it, a.spin_limit, a.err);
+      __syncthreads();
+      break;
+    }
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+
+    const SplitShared sm{sStage, sWP, sWT, sCnt, sRun};
+    split_tile<SB, THREADS>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+    pre = pre_next;
   }
 }
 
