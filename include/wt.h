@@ -188,6 +188,55 @@ int wt_free(wt_tree *tree);
 int wt_kernels_per_build(const wt_tree *tree);
 
 /*
+ * Batched construction of many independent trees (one persistent launch).
+ *
+ * The trees of a batch are built by a single persistent kernel over a work
+ * list of (tree, phase, tile) items -- pre-pass tiles, one node-table item,
+ * split-pass tiles per level, last-level tiles -- ordered phase by phase
+ * across trees.  An item waits (bounded) only on its own tree's previous
+ * phase, through a per-tree completion counter; there is no grid-wide
+ * barrier.  Each tree gets exactly the outputs of wt_build (same layout,
+ * identical bits); parallelism across trees is the paper's observation that
+ * independent constructions are embarrassingly parallel, and inside a tree
+ * the passes are those of levelWT (Fig. 1).
+ *
+ *   wt_seq_desc        n, sigma, symbol_bytes of one sequence (limits as
+ *                      for wt_create).
+ *   wt_batch_create    allocate outputs and scratch for m sequences (one
+ *                      device allocation) and the work list.  cfg may be
+ *                      NULL; cfg->tile_threads (128 or 256) selects the CTA
+ *                      size of the batch kernel.
+ *   wt_batch_set_inputs
+ *                      record the m device input pointers (host array of
+ *                      pointers, each 16-byte aligned, else WT_ERR_ARG);
+ *                      synchronous copy of the pointer table.
+ *   wt_batch_build     enqueue the build of every tree: one memset and one
+ *                      kernel launch on `stream`; capturable in a CUDA graph.
+ *   wt_batch_sync      wait; returns 0 or the first device error of any tree.
+ *   wt_batch_tree      tree i as a wt_tree view for wt_info / wt_sync /
+ *                      wt_access / wt_rank / wt_select; owned by the batch
+ *                      (wt_free on a view returns WT_ERR_ARG).
+ *   wt_batch_free      release the batch and its views.
+ *   wt_build_batch     create + set_inputs + build.
+ */
+typedef struct {
+  uint64_t n;
+  uint32_t sigma;
+  uint32_t symbol_bytes;
+} wt_seq_desc;
+
+typedef struct wt_batch wt_batch; /* opaque, library-owned */
+
+int wt_batch_create(const wt_seq_desc *descs, uint32_t m, const wt_config *cfg, wt_batch **out);
+int wt_batch_set_inputs(wt_batch *batch, const void *const *d_seqs);
+int wt_batch_build(wt_batch *batch, void *stream);
+int wt_batch_sync(wt_batch *batch);
+int wt_batch_tree(wt_batch *batch, uint32_t i, wt_tree **tree);
+int wt_batch_free(wt_batch *batch);
+int wt_build_batch(const wt_seq_desc *descs, const void *const *d_seqs, uint32_t m,
+                   const wt_config *cfg, void *stream, wt_batch **out);
+
+/*
  * Allocation-free build.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory while they run --
  * code inside a CUDA graph capture whose mode forbids allocation, hosts whose

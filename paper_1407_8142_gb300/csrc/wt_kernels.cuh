@@ -1,0 +1,967 @@
+// Device code of the level passes, shared by the single-tree build
+// (wt_build.cu) and the batched build (wt_batch.cu).  Everything here has
+// internal linkage: each translation unit instantiates what it uses.
+#pragma once
+#include <cstdint>
+
+#include "wt_dev.cuh"
+#include "wt_internal.h"
+
+using namespace wtk;
+
+namespace {
+
+constexpr uint32_t kHistSmemMaxBins = 8192;
+constexpr uint32_t kScanThreads = 256;
+constexpr uint32_t kScanItems = 8;
+constexpr uint32_t kScanChunk = kScanThreads * kScanItems;
+constexpr uint32_t kDefaultSpin = 1u << 22;
+
+// ------------------------------------------------------------------ helpers
+template <int SB>
+__device__ __forceinline__ void load32(const uint8_t *g, uint32_t my0, uint32_t nv, uint32_t *u) {
+  if (my0 + 32 <= nv) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(g);
+#pragma unroll
+    for (int c = 0; c < 2 * SB; ++c) {
+      const uint4 v = __ldg(src + c);
+      u[4 * c + 0] = v.x;
+      u[4 * c + 1] = v.y;
+      u[4 * c + 2] = v.z;
+      u[4 * c + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8 * SB; ++i) u[i] = 0;
+    for (uint32_t q = 0; q < 32 && my0 + q < nv; ++q) {
+      uint32_t s;
+      if (SB == 1) s = g[q];
+      else if (SB == 2) s = reinterpret_cast<const uint16_t *>(g)[q];
+      else s = reinterpret_cast<const uint32_t *>(g)[q];
+      if (SB == 1) u[q >> 2] |= s << (8 * (q & 3));
+      else if (SB == 2) u[q >> 1] |= s << (16 * (q & 1));
+      else u[q] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t valid_mask(uint32_t my0, uint32_t nv) {
+  if (my0 + 32 <= nv) return 0xFFFFFFFFu;
+  if (my0 >= nv) return 0u;
+  return (1u << (nv - my0)) - 1u;
+}
+
+template <int SB>
+struct SymT;
+template <>
+struct SymT<1> { using type = uint8_t; };
+template <>
+struct SymT<2> { using type = uint16_t; };
+template <>
+struct SymT<4> { using type = uint32_t; };
+
+// Outputs of one level: its bitmap row, directory row and zero count.
+struct LevelOut {
+  uint32_t *bits;
+  unsigned long long *rank;
+  unsigned long long *zeros;
+};
+
+// Write the level's bitmap word, the directory entries that fall in this
+// thread's 32 positions, and (last tile) the level totals.  R = ones before
+// the tile, excl = ones before this thread within the tile.
+template <int THREADS>
+__device__ __forceinline__ void write_level(const LevelOut &o, uint32_t tile, uint32_t NT,
+                                            uint64_t start, uint32_t my0, uint32_t n, uint32_t NB,
+                                            uint64_t W, uint32_t word, uint32_t R, uint32_t excl,
+                                            uint32_t total) {
+  const uint64_t widx = (uint64_t)tile * THREADS + threadIdx.x;
+  if (widx < W) o.bits[widx] = word;
+  if ((threadIdx.x & 15) == 0 && start + my0 < n) o.rank[(start + my0) >> 9] = R + excl;
+  if (tile == NT - 1 && threadIdx.x == 0) {
+    o.rank[NB] = R + total;
+    *o.zeros = (unsigned long long)(n - (R + total));
+  }
+}
+
+// ------------------------------------------------------------------ tile pipeline
+// Every level pass runs persistent CTAs that take tiles of T = 32*THREADS
+// symbols by ticket.  Tickets are fetched two tiles ahead, a tile's symbols
+// are copied into shared memory by the TMA engine one tile ahead (double
+// buffer), and the loads of a tile's count prefix are issued one tile ahead,
+// so no round trip to memory sits between two tiles of a CTA.
+template <int SB, int THREADS>
+struct TilePipe {
+  static constexpr uint32_t T = 32 * THREADS;
+  static constexpr uint32_t TB = T * SB;
+  uint8_t *sIn0, *sIn1;
+  uint64_t *bar;       // 2 mbarriers
+  uint32_t *ring;      // 3 tickets
+  const uint8_t *in;   // this level's symbols, 16-byte aligned
+  int in_padded;       // in holds whole tiles -> copy whole tiles
+  uint32_t n, NT;
+  uint32_t *ticket;
+
+  __device__ __forceinline__ void issue(uint32_t tile, int buf) const {
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, n - start);
+    const uint32_t bytes = in_padded ? TB : ((nv * SB) & ~15u);
+    mbar_arrive_expect_tx(&bar[buf], bytes);
+    if (bytes) bulk_g2s(buf ? sIn1 : sIn0, in + start * SB, bytes, &bar[buf]);
+  }
+  // thread 0, before the first __syncthreads
+  __device__ __forceinline__ void prologue() const {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    const uint32_t t0 = atomicAdd(ticket, 1u);
+    const uint32_t t1 = atomicAdd(ticket, 1u);
+    ring[0] = t0;
+    ring[1] = t1;
+    if (t0 < NT) issue(t0, 0);
+  }
+  // thread 0 at the top of iteration `it`: fetch the ticket of tile it+2
+  // (returned, stored at the end of the iteration) and start the copy of
+  // tile it+1
+  __device__ __forceinline__ uint32_t advance(uint32_t it, uint32_t nxt) const {
+    const uint32_t nn = atomicAdd(ticket, 1u);
+    if (nxt < NT) {
+      fence_proxy_async_smem();
+      issue(nxt, (it + 1) & 1);
+    }
+    return nn;
+  }
+  // all threads: wait for tile `it`'s symbols (bounded); false on timeout
+  __device__ __forceinline__ bool wait(uint32_t it, uint32_t spin, int *err) const {
+    return mbar_wait_bounded(&bar[it & 1], (it >> 1) & 1u, spin, err);
+  }
+  // after a timeout: wait (bounded) for the copies this CTA started
+  __device__ __forceinline__ void drain(uint32_t it, uint32_t spin, int *err) const {
+    if (threadIdx.x == 0) {
+      mbar_wait_bounded(&bar[it & 1], (it >> 1) & 1u, spin, err);
+      if (ring[(it + 1) % 3] < NT) mbar_wait_bounded(&bar[(it + 1) & 1], ((it + 1) >> 1) & 1u, spin, err);
+    }
+  }
+  __device__ __forceinline__ uint8_t *data(uint32_t it) const { return (it & 1) ? sIn1 : sIn0; }
+  // tail bytes of an unpadded input that the bulk copy (multiple of 16 bytes) left out
+  __device__ __forceinline__ bool fill_tail(uint8_t *sIn, uint64_t start, uint32_t nv) const {
+    if (in_padded || ((nv * SB) & 15u) == 0) return false;
+    for (uint32_t i = ((nv * SB) & ~15u) + threadIdx.x; i < nv * SB; i += THREADS)
+      sIn[i] = in[start * SB + i];
+    return true;
+  }
+};
+
+// This thread's part of the count-prefix of `tile`, loads issued now and
+// summed later (up to 3 terms per thread: tile < 2^20 and THREADS >= 128).
+struct PrefixLoads {
+  uint32_t v0, v1, v2;
+  __device__ __forceinline__ uint32_t sum() const { return v0 + v1 + v2; }
+};
+
+template <int THREADS>
+__device__ __forceinline__ PrefixLoads prefix_loads(const TileCounts &c, uint32_t tile, uint32_t NT) {
+  PrefixLoads p{0, 0, 0};
+  if (tile >= NT) return p;
+  const uint32_t nt = prefix_terms(tile), j = threadIdx.x;
+  if (j < nt) p.v0 = __ldcg(prefix_term(c, tile, j));
+  if (j + THREADS < nt) p.v1 = __ldcg(prefix_term(c, tile, j + THREADS));
+  if (j + 2 * THREADS < nt) p.v2 = __ldcg(prefix_term(c, tile, j + 2 * THREADS));
+  return p;
+}
+
+template <int SB, int THREADS>
+__device__ __forceinline__ void load_from_smem(const uint8_t *sIn, uint32_t my0, uint32_t *u) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(sIn + my0 * SB);
+#pragma unroll
+  for (int c = 0; c < 2 * SB; ++c) {
+    const uint4 v = src[c];
+    u[4 * c + 0] = v.x;
+    u[4 * c + 1] = v.y;
+    u[4 * c + 2] = v.z;
+    u[4 * c + 3] = v.w;
+  }
+}
+
+template <int SB, int THREADS>
+constexpr uint32_t pipe_smem_bytes() {
+  return 2u * 32u * THREADS * SB;
+}
+
+// ------------------------------------------------------------------ pre-pass
+struct PrepassArgs {
+  const uint8_t *in;  // S, 16-byte aligned
+  int in_padded;
+  uint32_t n, L, NT, sigma;
+  uint32_t *hist;     // 2^L bins
+  TileCounts cnt;     // level-0 ones per tile
+  uint32_t *ticket;
+  uint32_t spin_limit;
+  int *err;
+};
+
+template <int SB, int THREADS>
+constexpr uint32_t prepass_smem_bytes(uint32_t hist_bins) {
+  return pipe_smem_bytes<SB, THREADS>() + 4u * hist_bins + 64u;
+}
+
+// One pre-pass tile: symbol histogram (shared-memory bins when HIST_SMEM,
+// else warp-aggregated global atomics), range check (into `bad`) and the
+// level-0 ones of the tile.  Ends with a block barrier, after which thread 0
+// has stored ring_value to *ring_slot (if non-null).
+template <int SB, int THREADS, bool HIST_SMEM>
+__device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile, const uint8_t *sIn,
+                                           uint32_t *s_hist, uint32_t *s_wt, uint32_t &bad,
+                                           uint32_t *ring_slot, uint32_t ring_value) {
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t NW = THREADS / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lmask = (1u << a.L) - 1u;
+  const uint64_t start = (uint64_t)tile * T;
+  const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+  const uint32_t my0 = 32 * tid;
+  uint32_t u[8 * SB];
+  load_from_smem<SB, THREADS>(sIn, my0, u);
+  const uint32_t word = a.L ? pack_bits<SB>(u, a.L - 1) & valid_mask(my0, nv) : 0u;
+  if (__all_sync(0xFFFFFFFFu, my0 + 32 <= nv)) {  // warp-uniform: the loop uses warp collectives
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+      const uint32_t s = symbol_at<SB>(u, q);
+      bad |= (uint32_t)(s >= a.sigma);
+      if (HIST_SMEM) {
+        atomicAdd(&s_hist[s & lmask], 1u);
+      } else {
+        const uint32_t v = s & lmask;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, v);
+        if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
+      }
+    }
+  } else {
+    for (int q = 0; q < 32; ++q) {
+      const bool valid = my0 + q < nv;
+      const uint32_t s = symbol_at<SB>(u, q);
+      if (valid) bad |= (uint32_t)(s >= a.sigma);
+      if (HIST_SMEM) {
+        if (valid) atomicAdd(&s_hist[s & lmask], 1u);
+      } else {
+        const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
+        if (valid) {
+          const uint32_t v = s & lmask;
+          const uint32_t peers = __match_any_sync(am, v);
+          if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
+        }
+      }
+    }
+  }
+  const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, __popc(word));
+  if (lane == 0) s_wt[warp] = wsum;
+  __syncthreads();
+  if (warp == 0 && a.L) {
+    const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, lane < NW ? s_wt[lane] : 0u);
+    if (lane == 0) {
+      a.cnt.c0[tile] = total;
+      if (total) {
+        atomicAdd(&a.cnt.c1[tile >> 6], total);
+        atomicAdd(&a.cnt.c2[tile >> 12], total);
+      }
+    }
+  }
+  if (ring_slot) *ring_slot = ring_value;
+  __syncthreads();
+}
+
+// Reads S once: the 2^L-bin histogram (node sizes of every level), the range
+// check, and the level-0 ones of every tile.
+template <int SB, int THREADS, bool HIST_SMEM>
+__global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
+  constexpr uint32_t T = 32 * THREADS;
+  extern __shared__ __align__(128) uint8_t smem[];
+  TilePipe<SB, THREADS> pipe;
+  const uint32_t nbins = 1u << a.L;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint32_t *const s_hist = reinterpret_cast<uint32_t *>(smem + 2 * pipe.TB);
+  uint64_t *const bar = reinterpret_cast<uint64_t *>(s_hist + (HIST_SMEM ? ((nbins + 1) & ~1u) : 0));
+  pipe.bar = bar;
+  pipe.ring = reinterpret_cast<uint32_t *>(bar + 2);
+  uint32_t *const s_wt = pipe.ring + 4;  // ones per warp
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
+  const uint32_t tid = threadIdx.x;
+  uint32_t bad = 0;
+  if (HIST_SMEM)
+    for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
+  if (tid == 0) pipe.prologue();
+  __syncthreads();
+
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = pipe.ring[it % 3];
+    if (tile >= a.NT) break;
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = pipe.advance(it, nxt);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
+    if (__syncthreads_or(!ok)) {
+      pipe.drain(it, a.spin_limit, a.err);
+      __syncthreads();
+      break;
+    }
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+    prepass_tile<SB, THREADS, HIST_SMEM>(a, tile, sIn, s_hist, s_wt, bad,
+                                         tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+  }
+  if (bad) latch_error(a.err, WT_ERR_SYMBOL);
+  if (HIST_SMEM) {
+    __syncthreads();
+    for (uint32_t i = tid; i < nbins; i += THREADS)
+      if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+  }
+}
+
+// ------------------------------------------------------------------ last level
+struct LeafArgs {
+  const uint8_t *in;  // T_{L-1}, 16-byte aligned
+  int in_padded;
+  uint32_t n, L, NT, NB;
+  uint64_t W;
+  LevelOut out;
+  TileCounts cnt;     // ones of this level per tile
+  uint32_t *ticket;
+  uint32_t spin_limit;
+  int *err;
+};
+
+template <int SB, int THREADS>
+constexpr uint32_t leaf_smem_bytes() {
+  return pipe_smem_bytes<SB, THREADS>() + 8u * (THREADS / 32) + 64u;
+}
+
+// One tile of the last level: bits and directory.  share_part is this
+// thread's part of the tile's ones-prefix.  Ends with a block barrier, after
+// which thread 0 has stored ring_value to *ring_slot (if non-null).
+template <int SB, int THREADS>
+__device__ __forceinline__ void leaf_tile(const LeafArgs &a, uint32_t tile, const uint8_t *sIn,
+                                          uint32_t share_part, uint2 *s_wt, uint32_t *ring_slot,
+                                          uint32_t ring_value) {
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t NW = THREADS / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t start = (uint64_t)tile * T;
+  const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    const uint32_t my0 = 32 * tid;
+  uint32_t u[8 * SB];
+  load_from_smem<SB, THREADS>(sIn, my0, u);
+  const uint32_t word = pack_bits<SB>(u, 0) & valid_mask(my0, nv);
+  const uint32_t pc = __popc(word);
+  uint32_t incl = pc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, share_part);
+  if (lane == 31) s_wt[warp] = make_uint2(incl, share);
+  __syncthreads();
+  const uint2 wv = lane < NW ? s_wt[lane] : make_uint2(0, 0);
+  const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);
+  const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
+  const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);
+  write_level<THREADS>(a.out, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + incl - pc, total);
+  if (ring_slot) *ring_slot = ring_value;
+  __syncthreads();
+}
+
+// Level L-1 (and level 0 when L = 1): bits and directory; its nodes have
+// range 2 and no children.
+template <int SB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_leaf(LeafArgs a) {
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t NW = THREADS / 32;
+  extern __shared__ __align__(128) uint8_t smem[];
+  TilePipe<SB, THREADS> pipe;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint2 *const s_wt = reinterpret_cast<uint2 *>(smem + 2 * pipe.TB);  // {ones, prefix share} per warp
+  pipe.bar = reinterpret_cast<uint64_t *>(s_wt + NW);
+  pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) pipe.prologue();
+  __syncthreads();
+  PrefixLoads pre = prefix_loads<THREADS>(a.cnt, pipe.ring[0], a.NT);
+
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = pipe.ring[it % 3];
+    if (tile >= a.NT) break;
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = pipe.advance(it, nxt);
+    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cnt, nxt, a.NT);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
+    if (__syncthreads_or(!ok)) {
+      pipe.drain(it, a.spin_limit, a.err);
+      __syncthreads();
+      break;
+    }
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+    leaf_tile<SB, THREADS>(a, tile, sIn, pre.sum(), s_wt, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+    pre = pre_next;
+  }
+}
+
+// ------------------------------------------------------------------ split pass
+struct SplitArgs {
+  const uint8_t *in;   // T_l, 16-byte aligned
+  uint8_t *out;        // T_{l+1}
+  int in_padded;       // in holds whole tiles (scratch buffer) -> copy whole tiles
+  uint32_t n, L, level, NT, NB, log2T;
+  uint64_t W;
+  const uint2 *tab;    // this level's {O_l[p], E_{l+1}[2p+1] - O_l[p]}
+  LevelOut lo;
+  TileCounts cin;      // ones of level l per tile of T_l
+  TileCounts cout;     // ones of level l+1 per tile of T_{l+1} (accumulated here)
+  uint32_t *ticket;
+  uint32_t spin_limit;
+  int *err;
+};
+
+// Bit k1 of the symbols packed in a 32-bit word, counted.
+template <int SB>
+__device__ __forceinline__ uint32_t count_bit(uint32_t w, uint32_t k1) {
+  if (SB == 1) return __popc((w >> k1) & 0x01010101u);
+  if (SB == 2) return __popc((w >> k1) & 0x00010001u);
+  return (w >> k1) & 1u;
+}
+
+// Copy one run of `len` bytes staged in shared memory at byte offset soff of
+// `stage` to global byte offset g of `gout`; executed by one warp.  The run
+// was staged so that soff = g (mod 16): every full 16-byte chunk is one
+// aligned shared load and one aligned global store; the unaligned head and
+// tail bytes are copied singly.  Bit k1 of the copied symbols is counted into
+// cnt_a (symbol positions before split_at) and cnt_b (from split_at on).
+// Writes past gend (n * SB) are dropped (reachable only after a device error).
+template <int SB>
+__device__ __forceinline__ void warp_copy_run(const uint8_t *stage, uint32_t soff, uint8_t *gout,
+                                              uint64_t g, uint32_t len, uint64_t gend,
+                                              uint32_t split_at, uint32_t mk1, uint32_t k1,
+                                              uint32_t &cnt_a, uint32_t &cnt_b) {
+  if (g >= gend) return;
+  if (g + len > gend) len = (uint32_t)(gend - g);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t head = min(len, (16u - ((uint32_t)g & 15u)) & 15u);
+  const uint32_t nch = (len - head) >> 4;
+  const uint32_t tail0 = head + (nch << 4);
+  const uint32_t nb = head + (len - tail0);  // single bytes: head, then tail
+  const uint32_t p0 = (uint32_t)(g / SB);    // symbol position of the run's first byte
+  if (lane < nb) {
+    const uint32_t o = lane < head ? lane : tail0 + (lane - head);
+    gout[g + o] = stage[soff + o];
+    if (o % SB == 0) {  // first byte of a symbol: count it
+      uint32_t v;
+      if (SB == 1) v = stage[soff + o];
+      else if (SB == 2) v = *reinterpret_cast<const uint16_t *>(stage + soff + o);
+      else v = *reinterpret_cast<const uint32_t *>(stage + soff + o);
+      const uint32_t one = (v >> k1) & 1u;
+      if (p0 + o / SB >= split_at) cnt_b += one;
+      else cnt_a += one;
+    }
+  }
+  const uint4 *src = reinterpret_cast<const uint4 *>(stage + soff + head);
+  uint4 *dst = reinterpret_cast<uint4 *>(gout + g + head);
+  const uint32_t pc0 = p0 + head / SB;  // symbol position of chunk 0
+  for (uint32_t c = lane; c < nch; c += 32) {
+    const uint4 v = src[c];
+    dst[c] = v;
+    const uint32_t ones = __popc(v.x & mk1) + __popc(v.y & mk1) + __popc(v.z & mk1) + __popc(v.w & mk1);
+    if (pc0 + c * (16 / SB) >= split_at) cnt_b += ones;
+    else cnt_a += ones;
+  }
+}
+
+
+// Store v (the low SB bytes) at shared address oa if bit != 0, else at za,
+// and advance that address by one symbol.  Predicated, branch-free.
+template <int SB>
+__device__ __forceinline__ void scatter_one(uint32_t bit, uint32_t &oa, uint32_t &za, uint32_t v) {
+  if (SB == 1) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u8 [%0], %3;\n\t@!p st.shared.u8 [%1], %3;\n\t"
+        "@p add.u32 %0, %0, 1;\n\t@!p add.u32 %1, %1, 1;\n\t}"
+        : "+r"(oa), "+r"(za)
+        : "r"(bit), "r"(v)
+        : "memory");
+  } else if (SB == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u16 [%0], %3;\n\t@!p st.shared.u16 [%1], %3;\n\t"
+        "@p add.u32 %0, %0, 2;\n\t@!p add.u32 %1, %1, 2;\n\t}"
+        : "+r"(oa), "+r"(za)
+        : "r"(bit), "h"((unsigned short)v)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+        "@p st.shared.u32 [%0], %3;\n\t@!p st.shared.u32 [%1], %3;\n\t"
+        "@p add.u32 %0, %0, 4;\n\t@!p add.u32 %1, %1, 4;\n\t}"
+        : "+r"(oa), "+r"(za)
+        : "r"(bit), "r"(v)
+        : "memory");
+  }
+}
+
+// per-warp staging: 1024 symbols plus room to align both runs to their
+// global 16-byte phase
+template <int SB>
+__host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * SB + 48u; }
+
+constexpr uint32_t kTabSmem = 1024;  // level tables up to this many nodes live in shared memory
+
+template <int SB, int THREADS>
+constexpr uint32_t split_smem_bytes() {
+  // two input tiles, per-warp staging, per-thread {bit word, warp-local
+  // ones-prefix}, per-warp {ones, prefix share}, the level table, mbarriers,
+  // tickets, run counters and run starts
+  return pipe_smem_bytes<SB, THREADS>() + (THREADS / 32) * stage_bytes<SB>() + 8u * THREADS +
+         8u * (THREADS / 32) + 8u * kTabSmem + 192u;
+}
+
+// Shared-memory working set of one split tile.
+struct SplitShared {
+  uint8_t *stage;  // per-warp staging areas
+  uint2 *wp;       // per thread {bit word, warp-local ones-prefix}
+  uint2 *wt;       // per warp {ones, prefix share}
+  uint32_t *cnt;   // 4 run counters
+  uint32_t *run;   // 2 run starts
+};
+
+// One tile of the split pass over level a.level: bits and directory of the
+// level, stable split into T_{level+1}, next-level ones per destination tile.
+// sIn holds the tile's symbols; share is this thread's part of the tile's
+// ones-prefix (summed over the block here).  Ends with a block barrier,
+// after which thread 0 has stored ring_value to *ring_slot (if non-null).
+template <int SB, int THREADS>
+__device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab, uint32_t tile,
+                                           const uint8_t *sIn, uint32_t share_part,
+                                           const SplitShared &sm, uint32_t *ring_slot,
+                                           uint32_t ring_value) {
+  using Sym = typename SymT<SB>::type;
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t NW = THREADS / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t k = a.L - 1 - a.level;   // bit of this level
+  const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
+  const uint32_t pshift = a.L - a.level;  // node prefix = symbol >> pshift
+  const uint32_t lmask = (1u << a.L) - 1u;
+  uint8_t *const stage = sm.stage + warp * stage_bytes<SB>();
+  Sym *const stageS = reinterpret_cast<Sym *>(stage);
+  uint2 *const sWP = sm.wp;
+  uint2 *const sWT = sm.wt;
+  uint32_t *const sCnt = sm.cnt;
+  uint32_t *const sRun = sm.run;
+  const uint64_t start = (uint64_t)tile * T;
+  const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+
+    // Pass A: 32 consecutive symbols per thread -> one bitmap word; warp scan
+    // of the ones.
+    const uint32_t my0 = 32 * tid;
+    uint32_t word;
+    {
+      uint32_t u[8 * SB];
+      load_from_smem<SB, THREADS>(sIn, my0, u);
+      word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
+    }
+    const uint32_t pc = __popc(word);
+    uint32_t incl = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    const uint32_t pw = incl - pc;  // ones before this word, within the warp
+    sWP[tid] = make_uint2(word, pw);
+    const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, share_part);
+    if (lane == 31) sWT[warp] = make_uint2(incl, share);
+    __syncthreads();
+    const uint2 wv = lane < NW ? sWT[lane] : make_uint2(0, 0);
+    const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);  // ones before the warp
+    const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
+    const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);                       // ones before the tile
+    write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + pw, total);
+
+    // Pass B: stable split of the warp's segment into its staging area,
+    // zeros first.  In step s lane i holds the G symbols at 32*G*s + G*i
+    // (one 64-bit shared load); their bits come from the bitmap word, the
+    // ones before them from the word prefix plus a popcount.  In a tile that
+    // lies in one node, each run is staged at the 16-byte phase of its
+    // destination in T_{l+1}, so that it is written with aligned 16-byte
+    // copies.
+    const uint32_t seg = 1024 * warp;
+    const uint32_t nvw = nv > seg ? min(nv - seg, 1024u) : 0u;  // symbols of this warp
+    const uint32_t tw = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t nzw = nvw - tw;                              // zeros of this warp
+    const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
+    const uint32_t pf = ((uint32_t)sInS[0] & lmask) >> pshift;
+    const uint32_t pl = ((uint32_t)sInS[nv - 1] & lmask) >> pshift;
+    const uint32_t Zb = (uint32_t)start - R;  // zeros of level l before the tile
+    const uint32_t Zw = Zb + seg - Pw;        // zeros of level l before the warp
+    const uint32_t Ow = R + Pw;               // ones of level l before the warp
+    const bool one_node = pf == pl;
+    uint32_t gz = 0, go = 0, zoff = 0, ooff = nzw * SB;  // destinations, staging offsets (bytes)
+    if (one_node) {
+      const uint2 tb = tab[pf];
+      gz = tb.x + Zw;
+      go = tb.y + Ow;
+      zoff = (gz * SB) & 15u;
+      ooff = ((zoff + nzw * SB + 15u) & ~15u) + ((go * SB) & 15u);
+    }
+    if (nvw) {
+      constexpr uint32_t G8 = 8 / SB;     // symbols per lane per step
+      constexpr uint32_t LPW8 = 32 / G8;  // lanes per bitmap word
+      const uint32_t wsub = lane / LPW8;
+      const uint32_t bo = (lane % LPW8) * G8;
+      const uint32_t lowmask = (1u << bo) - 1u;
+      const uint8_t *segIn = sIn + seg * SB;
+      Sym *const zS = reinterpret_cast<Sym *>(stage + zoff);
+      Sym *const oS = reinterpret_cast<Sym *>(stage + ooff);
+      if (nvw == 1024) {
+        // Each symbol goes to the running zero or one pointer of its lane:
+        // one predicate, two predicated stores, two predicated increments --
+        // no branch, whatever the bits.
+        const uint32_t zbase = smem_addr(zS), obase = smem_addr(oS);
+#pragma unroll 2
+        for (uint32_t s = 0; s < 32 / G8; ++s) {
+          const uint32_t pos0 = 32 * G8 * s + G8 * lane;
+          const uint2 wp = sWP[32 * warp + G8 * s + wsub];
+          const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
+          const uint32_t bits = wp.x >> bo;
+          const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the warp
+          uint32_t oa = obase + Rl * SB, za = zbase + (pos0 - Rl) * SB;
+#pragma unroll
+          for (uint32_t j = 0; j < G8; ++j) {
+            const uint32_t w = j < G8 / 2 ? grp.x : grp.y;
+            const uint32_t v = w >> (8 * SB * (j % (G8 / 2)));
+            scatter_one<SB>(bits & (1u << j), oa, za, v);
+          }
+        }
+      } else {
+        for (uint32_t s = 0; s < 32 / G8; ++s) {
+          const uint32_t pos0 = 32 * G8 * s + G8 * lane;
+          const uint2 wp = sWP[32 * warp + G8 * s + wsub];
+          const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
+          const uint32_t bits = wp.x >> bo;
+          const uint32_t Rl = wp.y + __popc(wp.x & lowmask);
+          uint32_t o = Rl, z = pos0 - Rl;
+          for (uint32_t j = 0; j < G8; ++j) {
+            if (pos0 + j < nvw) {
+              const uint32_t w = j < G8 / 2 ? grp.x : grp.y;
+              const Sym v = (Sym)(w >> (8 * SB * (j % (G8 / 2))));
+              const uint32_t b = (bits >> j) & 1u;
+              Sym *const dst = b ? oS + o : zS + z;
+              *dst = v;
+              o += b;
+              z += b ^ 1u;
+            }
+          }
+        }
+      }
+      __syncwarp();
+
+      // Phase 2: the warp writes its zeros and ones to T_{l+1}, counting the
+      // next level's ones per destination tile.
+      if (one_node) {
+        // the whole tile lies in one node: its zeros and ones are two runs
+        const uint2 tb = tab[pf];
+        const uint32_t r0 = tb.x + Zb, r1 = tb.y + R;  // where the tile's runs start
+        const uint32_t s0 = ((r0 >> a.log2T) + 1) << a.log2T, s1 = ((r1 >> a.log2T) + 1) << a.log2T;
+        const uint32_t mk1 = (SB == 1 ? 0x01010101u : SB == 2 ? 0x00010001u : 1u) << k1;
+        const uint64_t gend = (uint64_t)a.n * SB;
+        uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
+        warp_copy_run<SB>(stage, zoff, a.out, (uint64_t)gz * SB, nzw * SB, gend, s0, mk1, k1, c0a, c0b);
+        warp_copy_run<SB>(stage, ooff, a.out, (uint64_t)go * SB, tw * SB, gend, s1, mk1, k1, c1a, c1b);
+        const uint32_t v0 = __reduce_add_sync(0xFFFFFFFFu, c0a);
+        const uint32_t v1 = __reduce_add_sync(0xFFFFFFFFu, c0b);
+        const uint32_t v2 = __reduce_add_sync(0xFFFFFFFFu, c1a);
+        const uint32_t v3 = __reduce_add_sync(0xFFFFFFFFu, c1b);
+        if (lane == 0) {
+          if (v0) atomicAdd(&sCnt[0], v0);
+          if (v1) atomicAdd(&sCnt[1], v1);
+          if (v2) atomicAdd(&sCnt[2], v2);
+          if (v3) atomicAdd(&sCnt[3], v3);
+          if (warp == 0) {
+            sRun[0] = r0;
+            sRun[1] = r1;
+          }
+        }
+      } else {
+        Sym *outS = reinterpret_cast<Sym *>(a.out);
+        for (uint32_t base = 0; base < nvw; base += 32) {
+          const uint32_t kk = base + lane;
+          const bool valid = kk < nvw;
+          uint32_t dest = 0xFFFFFFFFu, bit = 0;
+          if (valid) {
+            const Sym s = stageS[kk];
+            const uint32_t p = ((uint32_t)s & lmask) >> pshift;
+            const uint2 tb = tab[p];
+            dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
+            if (dest < a.n) outS[dest] = s;
+            else dest = 0xFFFFFFFFu;
+            bit = ((uint32_t)s >> k1) & 1u;
+          }
+          const uint32_t dt = dest >> a.log2T;
+          const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit && dest != 0xFFFFFFFFu);
+          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dt);
+          const uint32_t c = __popc(ones & peers);
+          if (dest != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1) && c)
+            counts_add(a.cout, dt, c);
+        }
+      }
+    }
+    if (ring_slot) *ring_slot = ring_value;
+    __syncthreads();
+    if (tid < 4 && one_node) {
+      // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
+      const uint32_t v = sm.cnt[tid];
+      if (v) {
+        sm.cnt[tid] = 0;
+        const uint32_t dt = (sm.run[tid >> 1] >> a.log2T) + (tid & 1);
+        if (dt < a.NT) counts_add(a.cout, dt, v);
+      }
+    }
+}
+
+template <int SB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t NW = THREADS / 32;
+  extern __shared__ __align__(128) uint8_t smem[];
+  TilePipe<SB, THREADS> pipe;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint8_t *const sStage = smem + 2 * pipe.TB;
+  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());  // {word, prefix}
+  uint2 *const sWT = sWP + THREADS;                  // per warp {ones, prefix share}
+  uint2 *const sTab = sWT + NW;                      // level table (small levels)
+  pipe.bar = reinterpret_cast<uint64_t *>(sTab + kTabSmem);
+  pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
+  uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
+  uint32_t *const sRun = sCnt + 4;                   // 2 run starts
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
+
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nodes = 1u << a.level;
+  const bool tab_smem = nodes <= kTabSmem;
+  const uint2 *const tab = tab_smem ? sTab : a.tab;
+
+  if (tab_smem)
+    for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
+  if (tid < 4) sCnt[tid] = 0;
+  if (tid == 0) pipe.prologue();
+  __syncthreads();
+  PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
+
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = pipe.ring[it % 3];
+    if (tile >= a.NT) break;
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = pipe.advance(it, nxt);
+    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
+    if (__syncthreads_or(!ok)) {
+      pipe.drain(it, a.spin_limit, a.err);
+      __syncthreads();
+      break;
+    }
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+
+    const SplitShared sm{sStage, sWP, sWT, sCnt, sRun};
+    split_tile<SB, THREADS>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+    pre = pre_next;
+  }
+}
+
+// ------------------------------------------------------------------ tables
+struct ScanArgs {
+  const uint32_t *hist;
+  unsigned long long *E;  // 2^L + 1 entries
+  uint32_t nbins, nblocks;
+  uint32_t *ticket;
+  Lookback lb;
+};
+
+// E[v] = sum of hist[0..v), E[nbins] = total.
+__global__ void __launch_bounds__(kScanThreads) k_hist_scan(ScanArgs a) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_tile, s_P;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= a.nblocks) return;
+  const uint32_t base = tile * kScanChunk + tid * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    v[i] = base + i < a.nbins ? a.hist[base + i] : 0u;
+    sum += v[i];
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<kScanThreads>(sum, s_warp, &total);
+  if (tid < 32) {
+    const uint32_t P = lookback(a.lb, tile, 0, total);
+    if (tid == 0) s_P = P;
+  }
+  __syncthreads();
+  uint32_t run = s_P + excl;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    if (base + i < a.nbins) a.E[base + i] = run;
+    run += v[i];
+  }
+  if (tile == a.nblocks - 1 && tid == 0) a.E[a.nbins] = s_P + total;
+}
+
+struct TabArgs {
+  const unsigned long long *E;
+  uint2 *tab;
+  uint32_t L, nblocks;
+  uint32_t *ticket;
+  Lookback lb;
+};
+
+// For levels l = 0..L-2 and prefixes p < 2^l:
+//   c1(p) = E[(2p+2) << (L-l-1)] - E[(2p+1) << (L-l-1)]   (size of node 2p+1 on level l+1)
+//   O_l(p) = sum of c1 over prefixes < p                     (ones of level l before node p)
+//   tab[2^l - 1 + p] = {O_l(p), E[(2p+1) << (L-l-1)] - O_l(p)}
+// Blocks are numbered level by level; each level is one look-back segment.
+__global__ void __launch_bounds__(kScanThreads) k_level_tables(TabArgs a) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_tile, s_P;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= a.nblocks) return;
+  uint32_t l = 0, first = 0;
+  for (; l + 1 < a.L; ++l) {
+    const uint32_t nb = ((1u << l) + kScanChunk - 1) / kScanChunk;
+    if (tile < first + nb) break;
+    first += nb;
+  }
+  const uint32_t cnt = 1u << l;
+  const uint32_t sh = a.L - l - 1;
+  const uint32_t base = (tile - first) * kScanChunk + tid * kScanItems;
+  uint32_t c1[kScanItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    const uint32_t p = base + i;
+    c1[i] = p < cnt ? (uint32_t)(a.E[(uint64_t)(2 * p + 2) << sh] - a.E[(uint64_t)(2 * p + 1) << sh])
+                    : 0u;
+    sum += c1[i];
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<kScanThreads>(sum, s_warp, &total);
+  if (tid < 32) {
+    const uint32_t P = lookback(a.lb, tile, first, total);
+    if (tid == 0) s_P = P;
+  }
+  __syncthreads();
+  uint32_t O = s_P + excl;
+  uint2 *tl = a.tab + (cnt - 1);
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    const uint32_t p = base + i;
+    if (p < cnt) tl[p] = make_uint2(O, (uint32_t)a.E[(uint64_t)(2 * p + 1) << sh] - O);
+    O += c1[i];
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// Node starts and level tables of one tree, computed by one CTA (used by the
+// batched build, where each tree's tables are one work item):
+//   E[v] = sum of hist[0..v) for v <= 2^L;
+//   tab[2^l - 1 + p] = {O_l(p), E[(2p+1) << (L-l-1)] - O_l(p)} for l <= L-2,
+//   O_l(p) = sum over p' < p of (E[(2p'+2) << (L-l-1)] - E[(2p'+1) << (L-l-1)]).
+// Ends with a block barrier.
+template <int THREADS>
+__device__ void tables_one_cta(const uint32_t *hist, uint32_t L, unsigned long long *E, uint2 *tab,
+                               uint32_t *s_warp) {
+  constexpr uint32_t ITEMS = 8;
+  constexpr uint32_t CH = THREADS * ITEMS;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t nbins = 1u << L;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < nbins; base += CH) {
+    const uint32_t i0 = base + tid * ITEMS;
+    uint32_t v[ITEMS], sum = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < ITEMS; ++i) {
+      v[i] = i0 + i < nbins ? hist[i0 + i] : 0u;
+      sum += v[i];
+    }
+    uint32_t total;
+    uint32_t run = carry + block_exclusive_scan<THREADS>(sum, s_warp, &total);
+#pragma unroll
+    for (uint32_t i = 0; i < ITEMS; ++i) {
+      if (i0 + i < nbins) E[i0 + i] = run;
+      run += v[i];
+    }
+    carry += total;
+    __syncthreads();
+  }
+  if (tid == 0) E[nbins] = carry;
+  __syncthreads();
+  for (uint32_t l = 0; l + 1 < L; ++l) {
+    const uint32_t cnt = 1u << l, sh = L - l - 1;
+    uint2 *tl = tab + (cnt - 1);
+    carry = 0;
+    for (uint32_t base = 0; base < cnt; base += CH) {
+      const uint32_t p0 = base + tid * ITEMS;
+      uint32_t c1[ITEMS], sum = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < ITEMS; ++i) {
+        const uint32_t p = p0 + i;
+        c1[i] = p < cnt ? (uint32_t)(E[(uint64_t)(2 * p + 2) << sh] - E[(uint64_t)(2 * p + 1) << sh]) : 0u;
+        sum += c1[i];
+      }
+      uint32_t total;
+      uint32_t O = carry + block_exclusive_scan<THREADS>(sum, s_warp, &total);
+#pragma unroll
+      for (uint32_t i = 0; i < ITEMS; ++i) {
+        const uint32_t p = p0 + i;
+        if (p < cnt) tl[p] = make_uint2(O, (uint32_t)E[(uint64_t)(2 * p + 1) << sh] - O);
+        O += c1[i];
+      }
+      carry += total;
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace

@@ -73,7 +73,18 @@ SIGNATURES = {
     "wt_free": (ctypes.c_int, [P]),
     "wt_kernels_per_build": (ctypes.c_int, [P]),
     "wt_build_noalloc": (ctypes.c_int, [P, U64, U32, U32, P, P, P, P, P, P]),
+    "wt_batch_create": (ctypes.c_int, [P, U32, ctypes.POINTER(Config), ctypes.POINTER(P)]),
+    "wt_batch_set_inputs": (ctypes.c_int, [P, P]),
+    "wt_batch_build": (ctypes.c_int, [P, P]),
+    "wt_batch_sync": (ctypes.c_int, [P]),
+    "wt_batch_tree": (ctypes.c_int, [P, U32, ctypes.POINTER(P)]),
+    "wt_batch_free": (ctypes.c_int, [P]),
+    "wt_build_batch": (ctypes.c_int, [P, P, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
 }
+
+
+class SeqDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("sigma", ctypes.c_uint32), ("symbol_bytes", ctypes.c_uint32)]
 
 
 def library_path() -> str:
@@ -329,3 +340,73 @@ def build_tree(seq, sigma: int, **cfg) -> WaveletTree:
     else:
         n, b = seq.numel(), seq.element_size()
     return WaveletTree(n, sigma, b, **cfg).build(seq)
+
+
+class TreeView:
+    """A tree built as part of a batch (owned by the batch)."""
+
+    def __init__(self, handle: int, batch: "Batch"):
+        self.handle = handle
+        self._batch = batch
+
+    def info(self) -> Info:
+        return wt_info(self.handle)
+
+    def sync(self) -> int:
+        return wt_sync(self.handle)
+
+    to_host = WaveletTree.to_host
+    access = WaveletTree.access
+    rank = WaveletTree.rank
+    select = WaveletTree.select
+
+
+class Batch:
+    """Many independent trees built by one persistent launch (wt_batch_*)."""
+
+    def __init__(self, specs, tile_threads: int = 0, spin_limit: int = 0):
+        """specs: list of (n, sigma, symbol_bytes)."""
+        self.m = len(specs)
+        descs = (SeqDesc * self.m)(*[SeqDesc(n, s, b) for n, s, b in specs])
+        self.cfg = Config(tile_threads, 0, spin_limit, 0)
+        out = P()
+        _check(load().wt_batch_create(descs, self.m, ctypes.byref(self.cfg), ctypes.byref(out)),
+               "wt_batch_create")
+        self.handle = out.value
+        self._inputs = None
+
+    def set_inputs(self, seqs) -> None:
+        """seqs: CUDA tensors (16-byte aligned data pointers) or numpy arrays."""
+        ts = [_torch_symbols(x) for x in seqs]
+        ptrs = (P * self.m)(*[t.data_ptr() for t in ts])
+        _check(load().wt_batch_set_inputs(self.handle, ptrs), "wt_batch_set_inputs")
+        self._inputs = ts
+
+    def build(self, stream=None) -> None:
+        _check(load().wt_batch_build(self.handle, _stream_ptr(stream)), "wt_batch_build")
+
+    def sync(self) -> int:
+        return int(load().wt_batch_sync(self.handle))
+
+    def tree(self, i: int) -> TreeView:
+        out = P()
+        _check(load().wt_batch_tree(self.handle, i, ctypes.byref(out)), "wt_batch_tree")
+        return TreeView(out.value, self)
+
+    def free(self) -> None:
+        if getattr(self, "handle", None):
+            load().wt_batch_free(self.handle)
+            self.handle = None
+            self._inputs = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
