@@ -213,6 +213,7 @@ int wt_kernels_per_build(const wt_tree *tree);
  *   wt_batch_build     enqueue the build of every tree: one memset and one
  *                      kernel launch on `stream`; capturable in a CUDA graph.
  *   wt_batch_sync      wait; returns 0 or the first device error of any tree.
+ *   wt_batch_latencies per-tree completion times of the last build.
  *   wt_batch_tree      tree i as a wt_tree view for wt_info / wt_sync /
  *                      wt_access / wt_rank / wt_select; owned by the batch
  *                      (wt_free on a view returns WT_ERR_ARG).
@@ -232,6 +233,10 @@ int wt_batch_set_inputs(wt_batch *batch, const void *const *d_seqs);
 int wt_batch_build(wt_batch *batch, void *stream);
 int wt_batch_sync(wt_batch *batch);
 int wt_batch_tree(wt_batch *batch, uint32_t i, wt_tree **tree);
+/* Measurement: after a build, ns[i] = time from the start of the batch's
+ * first item to the completion of tree i's last item (GPU global timer),
+ * for i < m.  Synchronises the batch's stream. */
+int wt_batch_latencies(wt_batch *batch, uint64_t *ns);
 int wt_batch_free(wt_batch *batch);
 int wt_build_batch(const wt_seq_desc *descs, const void *const *d_seqs, uint32_t m,
                    const wt_config *cfg, void *stream, wt_batch **out);

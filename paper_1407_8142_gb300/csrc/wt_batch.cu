@@ -31,6 +31,8 @@ struct BTree {
   uint32_t counts_per_level;
   int *err;
   uint32_t *done;           // one completion counter per phase
+  uint32_t phases;
+  unsigned long long *t_done;  // global-timer stamp when the tree's last item completed
 };
 
 struct BatchArgs {
@@ -41,7 +43,14 @@ struct BatchArgs {
   uint32_t *ticket;
   uint32_t spin_limit;
   int *err;                   // batch-level error (timeouts of dependency waits)
+  unsigned long long *t_start;  // global-timer stamp when the first item started
 };
+
+__device__ __forceinline__ unsigned long long global_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t phase_items(const BTree &t, uint32_t phase) {
   return phase == 1 ? 1u : t.NT;
@@ -182,6 +191,7 @@ __global__ void __launch_bounds__(THREADS) k_batch(BatchArgs a) {
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= a.n_items) break;
+    if (item == 0 && tid == 0) *a.t_start = global_timer();
     // group of this item: last g with grp_first[g] <= item
     uint32_t lo = 0, hi = a.n_groups - 1;
     while (lo < hi) {
@@ -254,7 +264,8 @@ __global__ void __launch_bounds__(THREADS) k_batch(BatchArgs a) {
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      atomicAdd(&tr.done[phase], 1u);
+      const uint32_t prev = atomicAdd(&tr.done[phase], 1u);
+      if (phase + 1 == tr.phases && prev + 1 == phase_items(tr, phase)) *tr.t_done = global_timer();
     }
   }
 }
@@ -370,7 +381,7 @@ int wt_batch_create(const wt_seq_desc *descs, uint32_t m, const wt_config *cfg, 
     g.cpl = g.NT + (g.NT >> 6) + 1 + (g.NT >> 12) + 1;
     g.phases = g.L >= 1 ? g.L + 2 : 2;
     // control block: error word, histogram, tile counts, phase counters
-    g.ctrl = al256((1 + g.nbins + Lz * g.cpl + g.phases) * 4);
+    g.ctrl = al256((1 + g.nbins + Lz * g.cpl + g.phases) * 4 + 16);
     mem += g.bits + g.rank + g.zeros + g.ns + g.tab + 2 * g.buf;
     ctrl += g.ctrl;
   }
@@ -413,6 +424,9 @@ int wt_batch_create(const wt_seq_desc *descs, uint32_t m, const wt_config *cfg, 
     t.hist = c + 1;
     t.counts = c + 1 + g.nbins;
     t.done = t.counts + std::max<uint32_t>(g.L, 1) * g.cpl;
+    t.phases = g.phases;
+    t.t_done = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(t.done + g.phases) + 7) & ~uintptr_t(7));
     coff += g.ctrl;
     t.n = (uint32_t)g.n;
     t.L = g.L;
@@ -499,6 +513,7 @@ int wt_batch_build(wt_batch *b, void *stream) {
   a.ticket = b->d_ctrl;
   a.spin_limit = b->cfg.spin_limit ? b->cfg.spin_limit : (1u << 22);
   a.err = reinterpret_cast<int *>(b->d_ctrl + 1);
+  a.t_start = reinterpret_cast<unsigned long long *>(b->d_ctrl + 2);
   auto launch = [&](auto kern, uint32_t threads, size_t sm) -> int {
     WT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int occ = 0;
@@ -531,6 +546,19 @@ int wt_batch_sync(wt_batch *b) {
   int be = 0;
   WT_CUDA(cudaMemcpy(&be, b->d_ctrl + 1, sizeof(int), cudaMemcpyDeviceToHost));
   return first ? first : be;
+}
+
+int wt_batch_latencies(wt_batch *b, uint64_t *ns) {
+  if (!b || !ns) return WT_ERR_ARG;
+  WT_CUDA(cudaStreamSynchronize(b->stream));
+  unsigned long long t0 = 0;
+  WT_CUDA(cudaMemcpy(&t0, b->d_ctrl + 2, 8, cudaMemcpyDeviceToHost));
+  for (uint32_t i = 0; i < b->m; ++i) {
+    unsigned long long t = 0;
+    WT_CUDA(cudaMemcpy(&t, b->host_trees[i].t_done, 8, cudaMemcpyDeviceToHost));
+    ns[i] = t >= t0 ? t - t0 : 0;
+  }
+  return WT_OK;
 }
 
 int wt_batch_tree(wt_batch *b, uint32_t i, wt_tree **tree) {

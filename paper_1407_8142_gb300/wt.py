@@ -78,6 +78,7 @@ SIGNATURES = {
     "wt_batch_build": (ctypes.c_int, [P, P]),
     "wt_batch_sync": (ctypes.c_int, [P]),
     "wt_batch_tree": (ctypes.c_int, [P, U32, ctypes.POINTER(P)]),
+    "wt_batch_latencies": (ctypes.c_int, [P, P]),
     "wt_batch_free": (ctypes.c_int, [P]),
     "wt_build_batch": (ctypes.c_int, [P, P, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
 }
@@ -387,6 +388,12 @@ class Batch:
 
     def sync(self) -> int:
         return int(load().wt_batch_sync(self.handle))
+
+    def latencies_ns(self) -> np.ndarray:
+        """Per-tree completion times of the last build (ns from batch start)."""
+        out = np.zeros(self.m, dtype=np.uint64)
+        _check(load().wt_batch_latencies(self.handle, out.ctypes.data), "wt_batch_latencies")
+        return out
 
     def tree(self, i: int) -> TreeView:
         out = P()
