@@ -242,6 +242,51 @@ int wt_build_batch(const wt_seq_desc *descs, const void *const *d_seqs, uint32_t
                    const wt_config *cfg, void *stream, wt_batch **out);
 
 /*
+ * Build server: continuous batching of build requests under an HBM budget.
+ *
+ * A worker thread admits queued requests in arrival order as soon as a
+ * request's footprint (its input copy, outputs, scratch and control block)
+ * fits in a device arena of `budget_bytes` (allocated once at creation) and
+ * one of `max_inflight` streams is free; all requests admissible at that
+ * moment form one batch (one launch of the batched build kernel).  Batches
+ * on different streams overlap on the device, so requests that arrive while
+ * others run start as soon as memory and a stream free up.  Results stay in
+ * the arena until released.  Each result is bit-identical to a wt_build of
+ * the same input.
+ *
+ *   wt_server_create   budget_bytes >= 1 MiB, 1 <= max_inflight <= 64; cfg may
+ *                      be NULL (tile_threads 128 or 256).  Uses the current
+ *                      device.
+ *   wt_server_submit   queue a build of h_seq[0..n) (host memory; page-locked
+ *                      memory copies asynchronously).  h_seq must stay valid
+ *                      until the request completes.  A request larger than
+ *                      the budget returns WT_ERR_ARG.
+ *   wt_server_poll     ids (and latencies, seconds from submit to completion
+ *                      on the device) of requests completed since the last
+ *                      poll, up to cap; *count gets their number.
+ *   wt_server_tree     the result of a completed request as a wt_tree view
+ *                      (owned by the server); returns its device status.
+ *   wt_server_release  free a completed request's memory (its view dies).
+ *   wt_server_drain    wait until every submitted request has completed.
+ *   wt_server_stats    out[0..5] = batches launched, requests admitted, peak
+ *                      arena bytes in use, bytes in use, budget, queued.
+ *   wt_server_free     stop the worker and release everything.
+ */
+typedef struct wt_server wt_server; /* opaque, library-owned */
+
+int wt_server_create(uint64_t budget_bytes, uint32_t max_inflight, const wt_config *cfg,
+                     wt_server **out);
+int wt_server_submit(wt_server *server, const void *h_seq, uint64_t n, uint32_t sigma,
+                     uint32_t symbol_bytes, uint64_t *id);
+int wt_server_poll(wt_server *server, uint64_t *ids, double *latency_s, uint32_t cap,
+                   uint32_t *count);
+int wt_server_tree(wt_server *server, uint64_t id, wt_tree **tree);
+int wt_server_release(wt_server *server, uint64_t id);
+int wt_server_drain(wt_server *server);
+int wt_server_stats(wt_server *server, uint64_t *out, uint32_t cap);
+int wt_server_free(wt_server *server);
+
+/*
  * Allocation-free build.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory while they run --
  * code inside a CUDA graph capture whose mode forbids allocation, hosts whose

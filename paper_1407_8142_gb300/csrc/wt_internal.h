@@ -48,7 +48,7 @@ struct wt_tree {
   uint32_t build_count = 0;
   cudaStream_t stream = nullptr;
   int sticky_error = 0;
-  wt_batch *owner = nullptr;      // set for views of trees built by a batch
+  void *owner = nullptr;          // set for views of trees owned by a batch or a server
 
   bool profile = false;
   cudaEvent_t *ev = nullptr;      // 2 * kMaxProfiled events, created on first use

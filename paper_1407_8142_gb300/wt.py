@@ -81,6 +81,14 @@ SIGNATURES = {
     "wt_batch_latencies": (ctypes.c_int, [P, P]),
     "wt_batch_free": (ctypes.c_int, [P]),
     "wt_build_batch": (ctypes.c_int, [P, P, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
+    "wt_server_create": (ctypes.c_int, [U64, U32, ctypes.POINTER(Config), ctypes.POINTER(P)]),
+    "wt_server_submit": (ctypes.c_int, [P, P, U64, U32, U32, ctypes.POINTER(U64)]),
+    "wt_server_poll": (ctypes.c_int, [P, P, P, U32, ctypes.POINTER(U32)]),
+    "wt_server_tree": (ctypes.c_int, [P, U64, ctypes.POINTER(P)]),
+    "wt_server_release": (ctypes.c_int, [P, U64]),
+    "wt_server_drain": (ctypes.c_int, [P]),
+    "wt_server_stats": (ctypes.c_int, [P, P, U32]),
+    "wt_server_free": (ctypes.c_int, [P]),
 }
 
 
@@ -405,6 +413,70 @@ class Batch:
             load().wt_batch_free(self.handle)
             self.handle = None
             self._inputs = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching build server (wt_server_*)."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 4, tile_threads: int = 0):
+        self.cfg = Config(tile_threads, 0, 0, 0)
+        out = P()
+        _check(load().wt_server_create(budget_bytes, max_inflight, ctypes.byref(self.cfg),
+                                       ctypes.byref(out)), "wt_server_create")
+        self.handle = out.value
+        self._ids = np.zeros(4096, dtype=np.uint64)
+        self._lat = np.zeros(4096, dtype=np.float64)
+
+    def submit(self, h_seq: np.ndarray, sigma: int) -> int:
+        """Queue a build of h_seq (keep it alive until the request completes)."""
+        rid = U64()
+        _check(load().wt_server_submit(self.handle, h_seq.ctypes.data, h_seq.size, sigma,
+                                       h_seq.dtype.itemsize, ctypes.byref(rid)), "wt_server_submit")
+        return int(rid.value)
+
+    def poll(self):
+        """[(id, latency_s)] of requests completed since the last poll."""
+        cnt = U32()
+        _check(load().wt_server_poll(self.handle, self._ids.ctypes.data, self._lat.ctypes.data,
+                                     self._ids.size, ctypes.byref(cnt)), "wt_server_poll")
+        k = int(cnt.value)
+        return list(zip(self._ids[:k].tolist(), self._lat[:k].tolist()))
+
+    def tree(self, rid: int):
+        out = P()
+        rc = load().wt_server_tree(self.handle, rid, ctypes.byref(out))
+        if rc == WT_ERR_ARG:
+            raise WTError(rc, "wt_server_tree")
+        return TreeView(out.value, self), rc
+
+    def release(self, rid: int) -> None:
+        _check(load().wt_server_release(self.handle, rid), "wt_server_release")
+
+    def drain(self) -> None:
+        _check(load().wt_server_drain(self.handle), "wt_server_drain")
+
+    def stats(self) -> dict:
+        out = np.zeros(6, dtype=np.uint64)
+        _check(load().wt_server_stats(self.handle, out.ctypes.data, 6), "wt_server_stats")
+        return dict(zip(["batches", "admitted", "peak_bytes", "used_bytes", "budget", "queued"],
+                        [int(x) for x in out]))
+
+    def free(self) -> None:
+        if getattr(self, "handle", None):
+            load().wt_server_free(self.handle)
+            self.handle = None
 
     def __enter__(self):
         return self

@@ -1,0 +1,91 @@
+"""Build server (continuous batching under an HBM budget).
+
+Every result built in the concurrent mix must be bit-identical to a
+standalone build of the same input; the budget must hold; requests that do
+not fit wait for memory instead of failing.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1407_8142_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1407_8142_gb300 import wt as mod
+    return mod
+
+
+def standalone(wt, S, sigma):
+    with wt.WaveletTree(S.size, sigma, S.dtype.itemsize) as t:
+        t.build(S)
+        return t.to_host()
+
+
+def test_results_equal_standalone_builds_in_the_mix(wt):
+    reqs = []
+    k = 0
+    for sigma, b in ((256, 1), (65536, 2), (1 << 20, 4), (5, 1)):
+        for n in (1000, 4097, 50000, 300001):
+            reqs.append((synth.zipf(n, sigma, 1.0, b, seed=k), sigma))
+            k += 1
+    # small budget: not everything fits at once, later requests wait for memory
+    budget = 64 << 20
+    with wt.Server(budget, max_inflight=3) as srv:
+        ids = []
+        for S, sg in reqs:
+            ids.append(srv.submit(S, sg))
+            time.sleep(0.0005)  # arrivals spread out: later ones join while earlier ones run
+        srv.drain()
+        done = {}
+        while len(done) < len(ids):
+            for rid, lat in srv.poll():
+                done[rid] = lat
+        assert sorted(done) == sorted(ids)
+        assert all(v >= 0 for v in done.values())
+        st = srv.stats()
+        assert st["admitted"] == len(reqs) and st["peak_bytes"] <= budget and st["batches"] >= 2
+        for rid, (S, sg) in zip(ids, reqs):
+            view, status = srv.tree(rid)
+            assert status == 0
+            got = view.to_host()
+            want = standalone(wt, S, sg)
+            assert np.array_equal(got["bits"], want["bits"])
+            assert np.array_equal(got["rank"], want["rank"])
+            assert np.array_equal(got["zeros"], want["zeros"])
+            assert np.array_equal(got["node_start"], want["node_start"])
+            srv.release(rid)
+        assert srv.stats()["used_bytes"] == 0
+
+
+def test_request_beyond_budget_is_rejected(wt):
+    with wt.Server(2 << 20, max_inflight=1) as srv:
+        big = np.zeros(4 << 20, dtype=np.uint8)
+        with pytest.raises(wt.WTError):
+            srv.submit(big, 256)
+        ok = synth.uniform(1000, 256, 1, 1)
+        rid = srv.submit(ok, 256)
+        srv.drain()
+        assert [r for r, _ in srv.poll()] == [rid]
+        srv.release(rid)
+
+
+def test_device_status_of_a_bad_request(wt):
+    with wt.Server(32 << 20, max_inflight=2) as srv:
+        bad = np.array([0, 1, 7, 3] * 100, dtype=np.uint8)  # 7 >= sigma = 5
+        good = synth.uniform(5000, 256, 1, 2)
+        r_bad = srv.submit(bad, 5)
+        r_good = srv.submit(good, 256)
+        srv.drain()
+        srv.poll()
+        assert srv.tree(r_bad)[1] == wt.WT_ERR_SYMBOL
+        assert srv.tree(r_good)[1] == 0
