@@ -465,6 +465,136 @@ def main_batch(args):
     return 0
 
 
+def serve_pools(seed):
+    """Pinned host pools of Zipf(1.0) symbols, one per alphabet class; every
+    request of the serving trace is a slice of its class's pool."""
+    import torch
+    from paper_1407_8142_gb300 import synth
+    pools = {}
+    for sigma, b in ((256, 1), (1 << 16, 2), (1 << 20, 4)):
+        h = synth.zipf(1 << 25, sigma, 1.0, b, seed + sigma)
+        view = {1: np.uint8, 2: np.int16, 4: np.int32}[b]
+        t = torch.from_numpy(h.view(view)).pin_memory()
+        pools[sigma] = (t, t.numpy().view({1: np.uint8, 2: np.uint16, 4: np.uint32}[b]))
+    return pools
+
+
+def serve_payloads(reqs, pools, seed):
+    from paper_1407_8142_gb300 import synth
+    out = []
+    for i, r in enumerate(reqs):
+        _, arr = pools[r["sigma"]]
+        span = arr.size - r["n"]
+        off = synth.splitmix64_scalar(seed, 777 + i) % (span + 1)
+        off -= off % 16  # 16-byte aligned slices of the pinned pool
+        out.append(arr[off:off + r["n"]])
+    return out
+
+
+def main_serve(args):
+    """Config 5: Poisson arrivals of build requests, continuous batching under
+    a 64 GB budget, versus one-at-a-time plain builds of the same trace."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1407_8142_gb300 import synth, wt
+    reqs = synth.config5_requests(rate=2000.0, horizon_s=args.serve_horizon, seed=args.seed)
+    m = len(reqs)
+    t0 = time.perf_counter()
+    pools = serve_pools(args.seed)
+    payloads = serve_payloads(reqs, pools, args.seed)
+    t_gen = time.perf_counter() - t0
+    total = sum(r["n"] for r in reqs)
+    arrivals = np.array([r["arrival_s"] for r in reqs])
+
+    # warm up the kernels once
+    with wt.Server(1 << 30, max_inflight=2, tile_threads=args.tile_threads) as w:
+        ids = [w.submit(p, r["sigma"]) for p, r in zip(payloads[:8], reqs[:8])]
+        w.drain()
+        for rid, _ in w.poll():
+            w.release(rid)
+
+    # continuous batching
+    lat = np.zeros(m)
+    done_t = np.zeros(m)
+    with wt.Server(64 << 30, max_inflight=args.serve_inflight, tile_threads=args.tile_threads) as srv:
+        id2i = {}
+        i = ndone = 0
+        with ClockSampler(0) as clocks:
+            start = time.perf_counter()
+            while ndone < m:
+                now = time.perf_counter() - start
+                while i < m and arrivals[i] <= now:
+                    id2i[srv.submit(payloads[i], reqs[i]["sigma"])] = i
+                    i += 1
+                got = srv.poll()
+                for rid, l in got:
+                    k = id2i[rid]
+                    lat[k] = l
+                    done_t[k] = time.perf_counter() - start
+                    if k % 997 == 0:  # parity sample: equal to a standalone build
+                        view, st = srv.tree(rid)
+                        a = view.to_host()
+                        with wt.WaveletTree(reqs[k]["n"], reqs[k]["sigma"], payloads[k].dtype.itemsize) as t:
+                            t.build(payloads[k])
+                            b_ = t.to_host()
+                        if st != 0 or not np.array_equal(a["bits"], b_["bits"]):
+                            raise SystemExit(f"served result {k} differs from a standalone build")
+                    srv.release(rid)
+                ndone += len(got)
+                if not got and i < m:
+                    time.sleep(max(0.0, min(arrivals[i] - (time.perf_counter() - start), 0.0002)))
+        stats = srv.stats()
+    makespan = float(done_t.max())
+
+    # one-at-a-time plain builds on the same trace (first-come first-served)
+    lat_p = []
+    start = time.perf_counter()
+    cap_s = args.serve_plain_cap
+    truncated = False
+    for k in range(m):
+        now = time.perf_counter() - start
+        if now < arrivals[k]:
+            time.sleep(arrivals[k] - now)
+        if time.perf_counter() - start > cap_s:
+            truncated = True
+            break
+        h = payloads[k]
+        view = {1: np.uint8, 2: np.int16, 4: np.int32}[h.dtype.itemsize]
+        d = torch.from_numpy(h.view(view)).to(dev, non_blocking=True)
+        t = wt.WaveletTree(h.size, reqs[k]["sigma"], h.dtype.itemsize)
+        t.build(d)
+        t.sync()
+        lat_p.append(time.perf_counter() - start - arrivals[k])
+        t.free()
+    plain_done = len(lat_p)
+    plain_makespan = time.perf_counter() - start
+    plain_symbols = sum(r["n"] for r in reqs[:plain_done])
+
+    line = {"metric": "served levelWT builds: input symbols/s and p50/p99 latency (arrival to result on device)",
+            "value": total / makespan, "unit": UNIT, "n_gpus": 1, "steps": m, "warmup": 1,
+            "ms_per_step": 1e3 * makespan / m, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/u16/u32", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals at 2000/s for %.0f s, n = floor(2^U(12,24)), sigma in "
+                                   "{256, 2^16, 2^20} (uint8/uint16/uint32), Zipf(1.0) symbols (slices of seeded pools), "
+                                   "64 GB HBM budget" % args.serve_horizon,
+                       "requests": m, "total_symbols": total, "max_inflight": args.serve_inflight,
+                       "offered_symbols_per_s": total / args.serve_horizon, "generate_s": round(t_gen, 1)},
+            "served": {"symbols_per_s": total / makespan, "makespan_s": makespan,
+                       "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                       "latency_ms_p99": 1e3 * float(np.percentile(lat, 99)),
+                       "batches": stats["batches"], "peak_hbm_bytes": stats["peak_bytes"]},
+            "plain_one_at_a_time": {"requests_done": plain_done, "truncated_at_s": cap_s if truncated else None,
+                                    "symbols_per_s": plain_symbols / plain_makespan, "makespan_s": plain_makespan,
+                                    "latency_ms_p50": 1e3 * float(np.percentile(lat_p, 50)) if lat_p else None,
+                                    "latency_ms_p99": 1e3 * float(np.percentile(lat_p, 99)) if lat_p else None},
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,9 +608,14 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["levelwt", "batch"], default="levelwt",
-                    help="levelwt: one build of n symbols (default); batch: the 4096-sequence batched build")
+    ap.add_argument("--workload", choices=["levelwt", "batch", "serve"], default="levelwt",
+                    help="levelwt: one build of n symbols (default); batch: the 4096-sequence batched "
+                         "build; serve: the request-serving trace")
     ap.add_argument("--batch-m", type=int, default=4096)
+    ap.add_argument("--serve-horizon", type=float, default=10.0)
+    ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-plain-cap", type=float, default=60.0,
+                    help="stop the one-at-a-time baseline after this many seconds")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
@@ -488,6 +623,8 @@ def main(argv=None):
         return main_reference(args)
     if args.workload == "batch":
         return main_batch(args)
+    if args.workload == "serve":
+        return main_serve(args)
     return main_ours(args)
 
 
