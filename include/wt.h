@@ -252,7 +252,9 @@ int wt_build_batch(const wt_seq_desc *descs, const void *const *d_seqs, uint32_t
  * on different streams overlap on the device, so requests that arrive while
  * others run start as soon as memory and a stream free up.  Results stay in
  * the arena until released.  Each result is bit-identical to a wt_build of
- * the same input.
+ * the same input.  A completed result holds its memory until it is
+ * released, so a client that keeps results must release them for queued
+ * requests to be admitted.
  *
  *   wt_server_create   budget_bytes >= 1 MiB, 1 <= max_inflight <= 64; cfg may
  *                      be NULL (tile_threads 128 or 256).  Uses the current
@@ -267,7 +269,10 @@ int wt_build_batch(const wt_seq_desc *descs, const void *const *d_seqs, uint32_t
  *   wt_server_tree     the result of a completed request as a wt_tree view
  *                      (owned by the server); returns its device status.
  *   wt_server_release  free a completed request's memory (its view dies).
- *   wt_server_drain    wait until every submitted request has completed.
+ *   wt_server_drain    wait until every submitted request has completed;
+ *                      WT_ERR_OOM when nothing is running and the next queued
+ *                      request cannot fit because completed results still hold
+ *                      the memory (release them and drain again).
  *   wt_server_stats    out[0..5] = batches launched, requests admitted, peak
  *                      arena bytes in use, bytes in use, budget, queued.
  *   wt_server_free     stop the worker and release everything.

@@ -123,6 +123,7 @@ struct wt_server {
   uint64_t next_id = 1;
   uint64_t in_flight = 0;
   bool stop = false;
+  bool blocked = false;   // nothing runs and the head of the queue does not fit
   int fatal = 0;
   std::thread worker;
   // statistics
@@ -242,6 +243,9 @@ void worker_main(wt_server *srv) {
         ++srv->admitted;
       }
       srv->peak_used = std::max(srv->peak_used, srv->arena.used());
+      bool any_busy = false;
+      for (const Slot &s2 : srv->slots) any_busy |= s2.busy;
+      srv->blocked = free_slot->ids.empty() && !any_busy && !srv->queue.empty();
       if (!free_slot->ids.empty()) {
         const int rc = launch_slot(srv, *free_slot);
         if (rc) srv->fatal = rc;
@@ -345,6 +349,7 @@ int wt_server_submit(wt_server *srv, const void *h_seq, uint64_t n, uint32_t sig
   const uint64_t rid = srv->next_id++;
   srv->reqs.emplace(rid, r);
   srv->queue.push_back(rid);
+  srv->blocked = false;
   ++srv->in_flight;
   *id = rid;
   return WT_OK;
@@ -390,14 +395,17 @@ int wt_server_release(wt_server *srv, uint64_t id) {
   srv->arena.release(it->second.off, it->second.bytes);
   delete it->second.view;
   srv->reqs.erase(it);
+  srv->blocked = false;  // memory freed: the worker re-evaluates admission
   return WT_OK;
 }
 
 int wt_server_drain(wt_server *srv) {
   if (!srv) return WT_ERR_ARG;
   std::unique_lock<std::mutex> lk(srv->mu);
-  srv->cv.wait(lk, [&] { return srv->in_flight == 0 || srv->fatal; });
-  return srv->fatal;
+  srv->cv.wait(lk, [&] { return srv->in_flight == 0 || srv->fatal || srv->blocked; });
+  if (srv->fatal) return srv->fatal;
+  // queued requests cannot be admitted until completed results are released
+  return srv->in_flight ? WT_ERR_OOM : WT_OK;
 }
 
 int wt_server_stats(wt_server *srv, uint64_t *out, uint32_t cap) {

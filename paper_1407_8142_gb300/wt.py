@@ -464,8 +464,12 @@ class Server:
     def release(self, rid: int) -> None:
         _check(load().wt_server_release(self.handle, rid), "wt_server_release")
 
-    def drain(self) -> None:
-        _check(load().wt_server_drain(self.handle), "wt_server_drain")
+    def drain(self) -> int:
+        """Wait for every request; WT_ERR_OOM if queued ones wait for releases."""
+        rc = int(load().wt_server_drain(self.handle))
+        if rc not in (WT_OK, WT_ERR_OOM):
+            raise WTError(rc, "wt_server_drain")
+        return rc
 
     def stats(self) -> dict:
         out = np.zeros(6, dtype=np.uint64)

@@ -38,33 +38,51 @@ def test_results_equal_standalone_builds_in_the_mix(wt):
         for n in (1000, 4097, 50000, 300001):
             reqs.append((synth.zipf(n, sigma, 1.0, b, seed=k), sigma))
             k += 1
-    # small budget: not everything fits at once, later requests wait for memory
+    # small budget: not everything fits at once, later requests wait for the
+    # memory of earlier results, which are checked and released as they complete
     budget = 64 << 20
     with wt.Server(budget, max_inflight=3) as srv:
-        ids = []
-        for S, sg in reqs:
-            ids.append(srv.submit(S, sg))
-            time.sleep(0.0005)  # arrivals spread out: later ones join while earlier ones run
-        srv.drain()
+        ids = {}
         done = {}
-        while len(done) < len(ids):
+
+        def collect():
             for rid, lat in srv.poll():
+                assert lat >= 0
+                S, sg = reqs[ids[rid]]
+                view, status = srv.tree(rid)
+                assert status == 0
+                got = view.to_host()
+                want = standalone(wt, S, sg)
+                assert np.array_equal(got["bits"], want["bits"])
+                assert np.array_equal(got["rank"], want["rank"])
+                assert np.array_equal(got["zeros"], want["zeros"])
+                assert np.array_equal(got["node_start"], want["node_start"])
+                srv.release(rid)
                 done[rid] = lat
-        assert sorted(done) == sorted(ids)
-        assert all(v >= 0 for v in done.values())
+
+        for k, (S, sg) in enumerate(reqs):
+            ids[srv.submit(S, sg)] = k
+            time.sleep(0.0005)  # arrivals spread out: later ones join while earlier ones run
+            collect()
+        deadline = time.time() + 120
+        while len(done) < len(reqs):
+            assert time.time() < deadline, "requests did not complete"
+            collect()
+            time.sleep(0.001)
         st = srv.stats()
         assert st["admitted"] == len(reqs) and st["peak_bytes"] <= budget and st["batches"] >= 2
-        for rid, (S, sg) in zip(ids, reqs):
-            view, status = srv.tree(rid)
-            assert status == 0
-            got = view.to_host()
-            want = standalone(wt, S, sg)
-            assert np.array_equal(got["bits"], want["bits"])
-            assert np.array_equal(got["rank"], want["rank"])
-            assert np.array_equal(got["zeros"], want["zeros"])
-            assert np.array_equal(got["node_start"], want["node_start"])
+        assert st["used_bytes"] == 0
+
+
+def test_drain_reports_memory_held_by_unreleased_results(wt):
+    big = [synth.uniform(200000, 1 << 20, 4, s) for s in range(4)]  # ~20 MB footprint each
+    with wt.Server(48 << 20, max_inflight=2) as srv:
+        rids = [srv.submit(S, 1 << 20) for S in big]
+        assert srv.drain() == wt.WT_ERR_OOM  # the later ones wait for memory
+        for rid, _ in srv.poll():
             srv.release(rid)
-        assert srv.stats()["used_bytes"] == 0
+        assert srv.drain() == wt.WT_OK
+        assert len(srv.poll()) + 2 >= len(rids)
 
 
 def test_request_beyond_budget_is_rejected(wt):
@@ -74,7 +92,7 @@ def test_request_beyond_budget_is_rejected(wt):
             srv.submit(big, 256)
         ok = synth.uniform(1000, 256, 1, 1)
         rid = srv.submit(ok, 256)
-        srv.drain()
+        assert srv.drain() == wt.WT_OK
         assert [r for r, _ in srv.poll()] == [rid]
         srv.release(rid)
 
