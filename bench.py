@@ -40,15 +40,36 @@ CPU_SAMPLE = 1 << 27       # cpu_baseline: first 2^27 symbols of the workload
 REF_STEP_SAMPLE = 1 << 23  # --impl reference: symbols per step
 
 
-def workload_config(extra=None):
-    cfg = {"workload": "plain levelWT at scale: n=2^30 uint8, sigma=256, Zipf(1.0) over a "
-                       "seeded id permutation, seed 0",
-           "n": N_SYMBOLS, "sigma": SIGMA, "symbol_bytes": SYMBOL_BYTES, "levels": 8,
-           "rank_directory": "512-bit blocks, uint64",
-           "l2": "inputs larger than L2 (1 GiB input, 2 GiB ping-pong, 1 GiB bitmaps)"}
+CONFIGS = {
+    1: {"n": 1 << 20, "sigma": 256, "b": 1, "levels": 8, "dtype": "u8",
+        "workload": "plain levelWT: n=2^20 uint8 symbols, i.i.d. uniform over sigma=256, seed 0",
+        "l2": "L2-resident working set (1 MiB input): GB/s are algorithmic bytes / time, not DRAM traffic"},
+    2: {"n": 1 << 30, "sigma": 256, "b": 1, "levels": 8, "dtype": "u8",
+        "workload": "plain levelWT at scale: n=2^30 uint8, sigma=256, Zipf(1.0) over a seeded id permutation, seed 0",
+        "l2": "inputs larger than L2 (1 GiB input, 2 GiB ping-pong, 1 GiB bitmaps)"},
+    3: {"n": 1 << 28, "sigma": 1 << 20, "b": 4, "levels": 20, "dtype": "u32",
+        "workload": "large alphabet: n=2^28 uint32, sigma=2^20 (20 levels), first half uniform, second half "
+                    "Zipf(1.2) over a seeded id permutation, seed 0",
+        "l2": "inputs larger than L2 (1 GiB input, 2 GiB ping-pong)"},
+}
+
+
+def config_input(cfg: int, n: int, seed: int) -> np.ndarray:
+    from paper_1407_8142_gb300 import synth
+    if cfg == 1:
+        return synth.uniform(n, 256, 1, seed)
+    if cfg == 3:
+        return synth.config3(seed, n=n)[0]
+    return synth.zipf(n, SIGMA, ZIPF_S, SYMBOL_BYTES, seed)
+
+
+def workload_config(extra=None, cfg: int = 2, n: int | None = None):
+    c = CONFIGS[cfg]
+    out = {"workload": c["workload"], "n": n or c["n"], "sigma": c["sigma"], "symbol_bytes": c["b"],
+           "levels": c["levels"], "rank_directory": "512-bit blocks, uint64", "l2": c["l2"]}
     if extra:
-        cfg.update(extra)
-    return cfg
+        out.update(extra)
+    return out
 
 
 def dist_env():
@@ -187,12 +208,12 @@ def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int) -> fl
     return 0.0
 
 
-def run_cpu_baseline(S: np.ndarray, sample: int):
+def run_cpu_baseline(S: np.ndarray, sample: int, sigma: int = SIGMA):
     from oracle import serialwt
     sub = np.ascontiguousarray(S[:sample])
     serialwt.build_oracle()
     t0 = time.perf_counter()
-    serialwt.build(sub, SIGMA)
+    serialwt.build(sub, sigma)
     dt = time.perf_counter() - t0
     return {"value": sub.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {sub.size} symbols of the workload (serialWT, 1 thread, gcc -O2)",
@@ -244,12 +265,14 @@ def main_ours(args):
     __graft_entry__.build()
     from paper_1407_8142_gb300 import synth, wt
 
-    n = args.n
+    C = CONFIGS[args.config]
+    sigma, sb = C["sigma"], C["b"]
+    n = args.n or C["n"]
     t_gen = time.perf_counter()
-    S = synth.zipf(n, SIGMA, ZIPF_S, SYMBOL_BYTES, args.seed + rank)
+    S = config_input(args.config, n, args.seed + rank)
     t_gen = time.perf_counter() - t_gen
-    d_S = torch.from_numpy(S).to(dev)
-    tree = wt.WaveletTree(n, SIGMA, SYMBOL_BYTES, tile_threads=args.tile_threads)
+    d_S = wt._torch_symbols(S)
+    tree = wt.WaveletTree(n, sigma, sb, tile_threads=args.tile_threads)
     stream = torch.cuda.current_stream(dev)
     inf = tree.info()
     L = inf.levels
@@ -294,20 +317,21 @@ def main_ours(args):
         per_kind[kind][0] += 1
         per_kind[kind][1] += ms
         if kind == "split":
-            split_bytes += algorithmic_bytes("split", level, n, SYMBOL_BYTES, L)
+            split_bytes += algorithmic_bytes("split", level, n, sb, L)
             split_ms += ms
             split_launches += 1
             level += 1
     total_kernel_ms = sum(v[1] for v in per_kind.values())
     peak, peak_kind = measured_hbm_peak()
     achieved = split_bytes / (split_ms * 1e-3) / 1e9 if split_ms else 0.0
-    build_bytes = (algorithmic_bytes("prepass", 0, n, SYMBOL_BYTES, L)
-                   + sum(algorithmic_bytes("split", l, n, SYMBOL_BYTES, L) for l in range(L - 1))
-                   + algorithmic_bytes("leaf", L - 1, n, SYMBOL_BYTES, L)
-                   + algorithmic_bytes("hist_scan", 0, n, SYMBOL_BYTES, L)
-                   + algorithmic_bytes("tables", 0, n, SYMBOL_BYTES, L))
+    build_bytes = (algorithmic_bytes("prepass", 0, n, sb, L)
+                   + sum(algorithmic_bytes("split", l, n, sb, L) for l in range(L - 1))
+                   + algorithmic_bytes("leaf", L - 1, n, sb, L)
+                   + algorithmic_bytes("hist_scan", 0, n, sb, L)
+                   + algorithmic_bytes("tables", 0, n, sb, L))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic() if args.config == 2 and n == CONFIGS[2]["n"] else None,
                 "kernel": "k_split (per-level split pass)",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy-based)",
                 "algorithmic_bytes_per_launch": split_bytes / max(split_launches, 1),
@@ -318,7 +342,7 @@ def main_ours(args):
     # end to end through the public host-buffer entry point
     e2e = None
     if not args.no_e2e:
-        h_S = torch.from_numpy(S).pin_memory()
+        h_S = torch.from_numpy(S.view({1: np.uint8, 2: np.int16, 4: np.int32}[sb])).pin_memory()
         NB = inf.blocks
         h_bits = torch.empty(L * inf.words_per_level, dtype=torch.int32).pin_memory()
         h_rank = torch.empty(L * (NB + 1), dtype=torch.int64).pin_memory()
@@ -334,28 +358,64 @@ def main_ours(args):
                 raise SystemExit(f"host build failed: {rc}")
         dt = (time.perf_counter() - t0) / e_steps
         dt = max_over_ranks(dt, ws, dev)
-        e2e = {"value": ws * n / dt, "unit": UNIT, "h2d_bytes_per_step": int(h_S.numel()),
+        e2e = {"value": ws * n / dt, "unit": UNIT, "h2d_bytes_per_step": int(h_S.numel() * sb),
                "d2h_bytes_per_step": int(h_bits.numel() * 4 + h_rank.numel() * 8),
                "steps": e_steps, "ms_per_step": dt * 1e3}
 
+    # small inputs: single-build latency, and builds replayed from one CUDA graph
+    latency = None
+    if args.config == 1:
+        s1, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        singles = []
+        for _ in range(20):
+            torch.cuda.synchronize(dev)
+            s1.record(stream)
+            tree.build(d_S, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            singles.append(s1.elapsed_time(e1))
+        R = 100
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                for _ in range(R):
+                    tree.build(d_S, side)
+        stream.wait_stream(side)
+        g.replay()
+        torch.cuda.synchronize(dev)
+        s1.record(stream)
+        for _ in range(5):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if tree.sync() != 0:
+            raise SystemExit("graph-replayed build failed")
+        per = s1.elapsed_time(e1) / (5 * R)
+        latency = {"single_build_ms_median": float(np.median(singles)),
+                   "graph_builds": R, "graph_build_ms": per, "graph_symbols_per_s": n / (per * 1e-3)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(S, min(args.cpu_sample, n))
+        cpu = run_cpu_baseline(S, min(args.cpu_sample, n), sigma)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "u8", "data": "synthetic",
+                "dtype": C["dtype"], "data": "synthetic",
                 "config": workload_config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                                            "tile_threads": args.tile_threads or "auto",
-                                           "generate_s": round(t_gen, 2)}),
+                                           "generate_s": round(t_gen, 2)}, cfg=args.config, n=n),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": kernels * args.steps,
                 "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4),
                                 "share": round(v[1] / total_kernel_ms, 4) if total_kernel_ms else None}
                             for k, v in per_kind.items()},
                 "clocks": clocks.summary()}
+        if latency:
+            line["latency"] = latency
         print(json.dumps(line), flush=True)
     tree.free()
     if ws > 1:
@@ -602,7 +662,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--n", type=int, default=N_SYMBOLS, help="symbols (default 2^30)")
+    ap.add_argument("--n", type=int, default=0, help="symbols (default: the configuration's n)")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3], default=2,
+                    help="1: n=2^20 uniform; 2: n=2^30 Zipf (default); 3: n=2^28 uint32, sigma=2^20")
     ap.add_argument("--tile-threads", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
