@@ -743,8 +743,17 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
     }
 }
 
+// Resident CTAs per SM the split pass is compiled for: as many as shared
+// memory allows, up to 48 warps per SM (caps registers at 42 per thread).
 template <int SB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_split(SplitArgs a) {
+constexpr int split_min_blocks() {
+  constexpr uint32_t by_smem = 232448u / split_smem_bytes<SB, THREADS>();
+  constexpr uint32_t by_warps = 1536u / THREADS;
+  return (int)(by_smem < by_warps ? (by_smem ? by_smem : 1u) : by_warps);
+}
+
+template <int SB, int THREADS>
+__global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_split(SplitArgs a) {
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t NW = THREADS / 32;
   extern __shared__ __align__(128) uint8_t smem[];
