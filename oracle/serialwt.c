@@ -34,6 +34,10 @@
  *   - zeros[l] = n - (number of 1 bits of level l).
  *   - The node table of Fig. 1 (Nodes[id] = bitmap offset, length), with the
  *     heap ids 2id+1 / 2id+2 for the children.
+ *   - The wavelet matrix of Section 7 (wto_matrix_build): per level, the
+ *     bitmap of bit (L-1-l) of the level's sequence and its zero count; the
+ *     next level's sequence is the stable reordering of the current one by
+ *     that bit, zeros first.  Same bit, directory and zero-count layout.
  *   - Queries by their definitions (Section 2): access(i) = S[i];
  *     rank_c(i) = #{j <= i : S[j] = c}; select_c(k) = position of the k-th
  *     occurrence of c (k counted from 1), by naive scans over S.
@@ -69,6 +73,26 @@ uint64_t wto_words_per_level(uint64_t n) { return 16ull * ((n + 511) / 512); }
 
 uint64_t wto_blocks(uint64_t n) { return (n + 511) / 512; }
 
+/* Rank directory and zero counts of every level, naively from the packed
+ * bits: rank[l*(NB+1) + k] = ones of level l before position 512k (k < NB),
+ * rank[l*(NB+1) + NB] = ones of level l, zeros[l] = n - ones of level l. */
+static void wto_directory(const uint32_t *bits, uint64_t n, uint32_t L, uint64_t *rank,
+                          uint64_t *zeros) {
+  const uint64_t W = wto_words_per_level(n);
+  const uint64_t NB = wto_blocks(n);
+  for (uint32_t l = 0; l < L; ++l) {
+    const uint32_t *B = bits + (uint64_t)l * W;
+    uint64_t *D = rank + (uint64_t)l * (NB + 1);
+    uint64_t ones = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if ((i & 511) == 0) D[i >> 9] = ones;
+      ones += (B[i >> 5] >> (i & 31)) & 1u;
+    }
+    D[NB] = ones;
+    zeros[l] = n - ones;
+  }
+}
+
 /* One entry of the node list A of Fig. 1: (start, len, id, range). */
 typedef struct {
   uint64_t start, len, id, range;
@@ -93,7 +117,6 @@ int wto_build(const void *S, uint64_t n, uint64_t sigma, uint32_t b,
 
   const uint32_t L = wto_levels(sigma);
   const uint64_t W = wto_words_per_level(n);
-  const uint64_t NB = wto_blocks(n);
   *n_nodes = 0;
   if (L == 0) return WTO_OK;
 
@@ -162,20 +185,54 @@ int wto_build(const void *S, uint64_t n, uint64_t sigma, uint32_t b,
     uint32_t *t = cur; cur = nxt; nxt = t;
   }
 
-  /* Rank directory and zero counts, naively from the packed bits. */
-  for (uint32_t l = 0; l < L; ++l) {
-    const uint32_t *B = bits + (uint64_t)l * W;
-    uint64_t *D = rank + (uint64_t)l * (NB + 1);
-    uint64_t ones = 0;
-    for (uint64_t i = 0; i < n; ++i) {
-      if ((i & 511) == 0) D[i >> 9] = ones;
-      ones += (B[i >> 5] >> (i & 31)) & 1u;
-    }
-    D[NB] = ones;
-    zeros[l] = n - ones;
-  }
-
+  wto_directory(bits, n, L, rank, zeros);
   free(cur); free(nxt); free(A); free(A2);
+  return WTO_OK;
+}
+
+/*
+ * The wavelet matrix of S (Section 7, after Claude and Navarro): level l's
+ * bitmap holds bit (L-1-l) of the symbols in the order T_l, where T_0 = S
+ * and T_{l+1} lists the symbols of T_l whose bit (L-1-l) is 0, in their T_l
+ * order, followed by those whose bit is 1, in their T_l order (the stable
+ * reordering by that bit).  zeros[l] is the number of 0 bits of level l;
+ * bits, rank and zeros have the layout of wto_build.  Plain sequential
+ * loops, one level after the other.
+ */
+int wto_matrix_build(const void *S, uint64_t n, uint64_t sigma, uint32_t b,
+                     uint32_t *bits, uint64_t *rank, uint64_t *zeros) {
+  if (!(b == 1 || b == 2 || b == 4) || sigma == 0) return WTO_ERR_ARG;
+  if (sigma > (1ull << (8 * b))) return WTO_ERR_ARG;
+  for (uint64_t i = 0; i < n; ++i)
+    if (sym_at(S, i, b) >= sigma) return WTO_ERR_SYMBOL;
+  const uint32_t L = wto_levels(sigma);
+  const uint64_t W = wto_words_per_level(n);
+  if (L == 0) return WTO_OK;
+  uint32_t *cur = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+  uint32_t *nxt = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+  if (!cur || !nxt) {
+    free(cur); free(nxt);
+    return WTO_ERR_OOM;
+  }
+  for (uint64_t i = 0; i < n; ++i) cur[i] = sym_at(S, i, b);
+  for (uint32_t l = 0; l < L; ++l) {
+    const uint32_t mask = 1u << (L - (l + 1));
+    uint32_t *B = bits + (uint64_t)l * W;
+    uint64_t z = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (cur[i] & mask) B[i >> 5] |= 1u << (i & 31);
+      else ++z;
+    }
+    /* zeros keep their order at the front, ones keep theirs behind them */
+    uint64_t lefts = 0, rights = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+      if (cur[i] & mask) nxt[z + rights++] = cur[i];
+      else nxt[lefts++] = cur[i];
+    }
+    uint32_t *t = cur; cur = nxt; nxt = t;
+  }
+  wto_directory(bits, n, L, rank, zeros);
+  free(cur); free(nxt);
   return WTO_OK;
 }
 

@@ -54,6 +54,8 @@ def _bind(path: str):
     lib.wto_levels.argtypes = [U64]
     lib.wto_build.restype = ctypes.c_int
     lib.wto_build.argtypes = [P, U64, U64, U32, P, P, P, P, P, P, U64, P]
+    lib.wto_matrix_build.restype = ctypes.c_int
+    lib.wto_matrix_build.argtypes = [P, U64, U64, U32, P, P, P]
     lib.wto_access.restype = None
     lib.wto_access.argtypes = [P, U64, U32, P, U64, P]
     lib.wto_rank.restype = None
@@ -147,6 +149,28 @@ def build(S: np.ndarray, sigma: int, lib=None) -> dict:
     k = int(nn[0])
     return {"L": L, "n": n, "sigma": sigma, "bits": bits, "rank": rank, "zeros": zeros,
             "node_id": node_id[:k], "node_start": node_start[:k], "node_len": node_len[:k]}
+
+
+def matrix_build(S: np.ndarray, sigma: int, lib=None) -> dict:
+    """The wavelet matrix of S (Section 7) with alphabet size sigma.
+
+    Returns a dict with ``L``, ``bits`` (L x W uint32), ``rank`` (L x (NB+1)
+    uint64) and ``zeros`` (L uint64), in the layout of ``build``.  The
+    queries of a wavelet matrix answer the same questions about S as those
+    of the tree, so ``access``/``rank``/``select`` below serve both.
+    Raises OracleError(ERR_SYMBOL) when a symbol is >= sigma.
+    """
+    lib = lib or _load()
+    S, b = _as_symbols(S)
+    n = int(S.size)
+    L = int(lib.wto_levels(sigma))
+    bits = np.zeros((L, words_per_level(n)), dtype=np.uint32)
+    rank = np.zeros((L, blocks(n) + 1), dtype=np.uint64)
+    zeros = np.zeros(L, dtype=np.uint64)
+    rc = lib.wto_matrix_build(_ptr(S), n, sigma, b, _ptr(bits), _ptr(rank), _ptr(zeros))
+    if rc != 0:
+        raise OracleError(rc)
+    return {"L": L, "n": n, "sigma": sigma, "bits": bits, "rank": rank, "zeros": zeros}
 
 
 def access(S: np.ndarray, idx: np.ndarray, lib=None) -> np.ndarray:

@@ -90,3 +90,59 @@ def test_planted_mistake_is_caught(oracle_mod, tmp_path, name, old, new):
     assert old in src, f"mutation site for '{name}' not found"
     lib = oracle_mod.compile_variant(src.replace(old, new), str(tmp_path / "m"))
     assert not pins_pass(oracle_mod, lib), f"planted mistake '{name}' was not caught"
+
+
+# Mistakes planted in the wavelet-matrix builder (Section 7); each site is
+# unique to it.
+MATRIX_MUTANTS = [
+    ("ones before zeros",
+     "if (cur[i] & mask) nxt[z + rights++] = cur[i];\n      else nxt[lefts++] = cur[i];",
+     "if (cur[i] & mask) nxt[rights++] = cur[i];\n      else nxt[(n - z) + lefts++] = cur[i];"),
+    ("unstable ones", "if (cur[i] & mask) nxt[z + rights++] = cur[i];",
+     "if (cur[i] & mask) nxt[n - 1 - rights++] = cur[i];"),
+    ("unstable zeros", "else nxt[lefts++] = cur[i];", "else nxt[z - 1 - lefts++] = cur[i];"),
+    ("no reordering between levels",
+     "    uint32_t *t = cur; cur = nxt; nxt = t;\n  }\n  wto_directory(bits, n, L, rank, zeros);\n  free(cur); free(nxt);\n",
+     "  }\n  wto_directory(bits, n, L, rank, zeros);\n  free(cur); free(nxt);\n"),
+    ("bit index from the bottom",
+     "const uint32_t mask = 1u << (L - (l + 1));\n    uint32_t *B = bits + (uint64_t)l * W;\n    uint64_t z = 0;",
+     "const uint32_t mask = 1u << l;\n    uint32_t *B = bits + (uint64_t)l * W;\n    uint64_t z = 0;"),
+]
+
+
+def matrix_pins_pass(o, lib) -> bool:
+    from tests.test_oracle_matrix_pins import mx_access, sorted_levels
+    try:
+        with open(os.path.join(HERE, "golden", "matrix_examples.json")) as f:
+            for e in json.load(f)["examples"]:
+                res = o.matrix_build(np.array(e["S"], dtype=np.uint8), e["sigma"], lib=lib)
+                if res["bits"][:, 0].tolist() != e["word0"] or res["zeros"].tolist() != e["zeros"]:
+                    return False
+                if res["rank"].tolist() != e["rank"]:
+                    return False
+        for sigma, b, n in ((256, 1, 1200), (11, 1, 300), (70000, 4, 500)):
+            S = synth.zipf(n, sigma, 1.0, b, 5)
+            res = o.matrix_build(S, sigma, lib=lib)
+            levels = [unpack(res["bits"][l], n).astype(np.int64) for l in range(res["L"])]
+            ref = sorted_levels(S, sigma)
+            if [lv.tolist() for lv in levels] != ref:
+                return False
+            zeros = [int(z) for z in res["zeros"]]
+            if [mx_access(levels, zeros, i) for i in range(0, n, 7)] != S[::7].astype(np.int64).tolist():
+                return False
+    except Exception:
+        return False
+    return True
+
+
+def test_matrix_original_passes(oracle_mod, tmp_path):
+    lib = oracle_mod.compile_variant(oracle_mod.source_text(), str(tmp_path / "orig"))
+    assert matrix_pins_pass(oracle_mod, lib)
+
+
+@pytest.mark.parametrize("name,old,new", MATRIX_MUTANTS, ids=[m[0] for m in MATRIX_MUTANTS])
+def test_matrix_planted_mistake_is_caught(oracle_mod, tmp_path, name, old, new):
+    src = oracle_mod.source_text()
+    assert src.count(old) == 1, f"mutation site for '{name}' not unique"
+    lib = oracle_mod.compile_variant(src.replace(old, new), str(tmp_path / "m"))
+    assert not matrix_pins_pass(oracle_mod, lib), f"planted mistake '{name}' was not caught"
