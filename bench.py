@@ -35,6 +35,7 @@ SIGMA = 256
 SYMBOL_BYTES = 1
 ZIPF_S = 1.0
 METRIC = "levelWT build throughput (input symbols/s)"
+MATRIX_METRIC = "wavelet matrix build throughput (input symbols/s)"
 UNIT = "symbols/s"
 CPU_SAMPLE = 1 << 27       # cpu_baseline: first 2^27 symbols of the workload
 REF_STEP_SAMPLE = 1 << 23  # --impl reference: symbols per step
@@ -193,11 +194,9 @@ def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int) -> fl
     NB = (n + 511) // 512
     bits = 16 * NB * 4
     directory = 8 * (NB + 1)
-    if kind == "prepass":
-        return n * b + bits + directory
-    if kind == "split":
-        if level_index == 0:          # level-0 bits come from the pre-pass
-            return 2 * n * b + 8 * NB
+    if kind == "prepass":             # reads S; tile counts and histogram are small
+        return n * b
+    if kind == "split":               # reads T_l, writes T_{l+1}, B_l and its directory
         return 2 * n * b + bits + directory
     if kind == "leaf":
         return n * b + bits + directory
@@ -208,15 +207,17 @@ def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int) -> fl
     return 0.0
 
 
-def run_cpu_baseline(S: np.ndarray, sample: int, sigma: int = SIGMA):
+def run_cpu_baseline(S: np.ndarray, sample: int, sigma: int = SIGMA, matrix: bool = False):
     from oracle import serialwt
     sub = np.ascontiguousarray(S[:sample])
     serialwt.build_oracle()
+    fn = serialwt.matrix_build if matrix else serialwt.build
     t0 = time.perf_counter()
-    serialwt.build(sub, sigma)
+    fn(sub, sigma)
     dt = time.perf_counter() - t0
+    what = "sequential wavelet matrix" if matrix else "serialWT"
     return {"value": sub.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {sub.size} symbols of the workload (serialWT, 1 thread, gcc -O2)",
+            "sample": f"first {sub.size} symbols of the workload ({what}, 1 thread, gcc -O2)",
             "seconds": dt}
 
 
@@ -230,15 +231,18 @@ def main_reference(args):
     from paper_1407_8142_gb300 import synth
     serialwt.build_oracle()
     S = synth.zipf(REF_STEP_SAMPLE, SIGMA, ZIPF_S, SYMBOL_BYTES, 0)
+    matrix = args.shape == "matrix"
+    fn = serialwt.matrix_build if matrix else serialwt.build
     for _ in range(args.warmup):
-        serialwt.build(S, SIGMA)
+        fn(S, SIGMA)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        serialwt.build(S, SIGMA)
+        fn(S, SIGMA)
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     value = S.size / dt
-    sample = f"first {S.size} symbols of the workload per step (serialWT, 1 thread)"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+    what = "sequential wavelet matrix" if matrix else "serialWT"
+    sample = f"first {S.size} symbols of the workload per step ({what}, 1 thread)"
+    line = {"impl": "reference", "metric": MATRIX_METRIC if matrix else METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -272,7 +276,8 @@ def main_ours(args):
     S = config_input(args.config, n, args.seed + rank)
     t_gen = time.perf_counter() - t_gen
     d_S = wt._torch_symbols(S)
-    tree = wt.WaveletTree(n, sigma, sb, tile_threads=args.tile_threads)
+    matrix = args.shape == "matrix"
+    tree = (wt.WaveletMatrix if matrix else wt.WaveletTree)(n, sigma, sb, tile_threads=args.tile_threads)
     stream = torch.cuda.current_stream(dev)
     inf = tree.info()
     L = inf.levels
@@ -326,12 +331,13 @@ def main_ours(args):
     achieved = split_bytes / (split_ms * 1e-3) / 1e9 if split_ms else 0.0
     build_bytes = (algorithmic_bytes("prepass", 0, n, sb, L)
                    + sum(algorithmic_bytes("split", l, n, sb, L) for l in range(L - 1))
-                   + algorithmic_bytes("leaf", L - 1, n, sb, L)
-                   + algorithmic_bytes("hist_scan", 0, n, sb, L)
-                   + algorithmic_bytes("tables", 0, n, sb, L))
+                   + algorithmic_bytes("leaf", L - 1, n, sb, L))
+    if not matrix:
+        build_bytes += algorithmic_bytes("hist_scan", 0, n, sb, L) + algorithmic_bytes("tables", 0, n, sb, L)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic() if args.config == 2 and n == CONFIGS[2]["n"] else None,
+                "traffic": (profiled_traffic() if args.config == 2 and n == CONFIGS[2]["n"] and not matrix
+                            else None),
                 "kernel": "k_split (per-level split pass)",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy-based)",
                 "algorithmic_bytes_per_launch": split_bytes / max(split_launches, 1),
@@ -398,14 +404,16 @@ def main_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(S, min(args.cpu_sample, n), sigma)
+        cpu = run_cpu_baseline(S, min(args.cpu_sample, n), sigma, matrix)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        line = {"metric": MATRIX_METRIC if matrix else METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": C["dtype"], "data": "synthetic",
-                "config": workload_config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                "config": workload_config({"structure": "wavelet matrix (Section 7)" if matrix
+                                           else "levelwise wavelet tree (Fig. 1)",
+                                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                                            "tile_threads": args.tile_threads or "auto",
                                            "generate_s": round(t_gen, 2)}, cfg=args.config, n=n),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -666,6 +674,8 @@ def main(argv=None):
     ap.add_argument("--config", type=int, choices=[1, 2, 3], default=2,
                     help="1: n=2^20 uniform; 2: n=2^30 Zipf (default); 3: n=2^28 uint32, sigma=2^20")
     ap.add_argument("--tile-threads", type=int, default=0)
+    ap.add_argument("--shape", choices=["tree", "matrix"], default="tree",
+                    help="levelwise wavelet tree (default) or wavelet matrix (Section 7)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
     ap.add_argument("--no-e2e", action="store_true")

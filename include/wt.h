@@ -46,6 +46,10 @@ extern "C" {
 
 typedef struct wt_tree wt_tree; /* opaque, library-owned */
 
+/* What a wt_tree object holds (wt_info_t.shape). */
+#define WT_SHAPE_TREE 0   /* levelwise wavelet tree (Sections 2 and 4) */
+#define WT_SHAPE_MATRIX 1 /* wavelet matrix (Section 7) */
+
 /*
  * Output layout, read through wt_info.  All pointers are device pointers
  * owned by the tree; callers read them and must not free them.
@@ -65,13 +69,19 @@ typedef struct wt_tree wt_tree; /* opaque, library-owned */
  *                node of prefix p on level l (Fig. 1's Nodes[2^l - 1 + p])
  *                starts at d_node_start[p << (L-l)] in that level's bitmap and
  *                has length d_node_start[(p+1) << (L-l)] - d_node_start[p << (L-l)].
+ *                NULL for a wavelet matrix.
+ *
+ * A wavelet matrix (shape WT_SHAPE_MATRIX, Section 7) has the same d_bits,
+ * d_rank and d_zeros layout; only the order T_l differs: T_{l+1} is the
+ * whole of T_l stably split by bit (L-1-l), all zeros first, and
+ * d_zeros[l] is the Z_l that the matrix's queries add to a 1-bit position.
  */
 typedef struct {
   uint64_t n;
   uint32_t sigma;
   uint32_t symbol_bytes;
   uint32_t levels;
-  uint32_t reserved;
+  uint32_t shape; /* WT_SHAPE_TREE or WT_SHAPE_MATRIX */
   uint64_t words_per_level;
   uint64_t blocks;
   uint32_t *d_bits;
@@ -112,10 +122,10 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
 
 /*
  * Enqueue the construction of `tree` from d_seq[0..n) on `stream` (levelWT,
- * Fig. 1): a pre-pass that histograms the symbols and writes level 0's bits
- * and directory, the node tables, one split pass per level l = 0..L-2
- * (bits, directory and the stable split into T_{l+1}), and a last pass for
- * level L-1.  Every size is known on the host, so the call has no host
+ * Fig. 1): a pre-pass that histograms the symbols, checks their range and
+ * counts level 0's ones per tile, the node tables, one split pass per level
+ * l = 0..L-2 (bits, directory and the stable split into T_{l+1}), and a last
+ * pass for level L-1 (bits and directory).  Every size is known on the host, so the call has no host
  * synchronisation and may be captured into a CUDA graph.
  * d_seq is read-only; it must stay valid until the stream work completes.
  * A d_seq that is not 16-byte aligned is first copied into tree scratch.
@@ -141,6 +151,26 @@ int wt_build_ex(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_b
 int wt_build_host(wt_tree *tree, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
                   void *stream);
 
+/*
+ * Wavelet matrix (Section 7).  Allocates like wt_create, without the
+ * histogram, node tables and d_node_start, for a wt_tree of shape
+ * WT_SHAPE_MATRIX.  Every other call taking a wt_tree (wt_rebuild,
+ * wt_build_host, wt_sync, wt_info, the queries, wt_profile, wt_free,
+ * wt_kernels_per_build) works on it unchanged.  Its construction is one
+ * pre-pass (range check, level-0 ones per tile), then per level
+ * l = 0..L-2 the split pass of the tree with a single node: zeros go to
+ * j - R(j), ones to Z_l + R(j), where Z_l is the level's zero count, known
+ * before the pass from the previous pass's tile counts.  The last level
+ * writes bits and directory only.
+ * Errors: as wt_create / wt_rebuild.
+ */
+int wt_matrix_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+                     wt_tree **out);
+
+/* wt_matrix_create followed by wt_rebuild.  cfg may be NULL. */
+int wt_matrix_build(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                    const wt_config *cfg, void *stream, wt_tree **out);
+
 /* Wait for the tree's last enqueued work and return its status. */
 int wt_sync(wt_tree *tree);
 
@@ -148,10 +178,12 @@ int wt_sync(wt_tree *tree);
 int wt_info(const wt_tree *tree, wt_info_t *info);
 
 /*
- * Batched queries over a built tree (Section 2 definitions), one result per
- * query, enqueued on `stream`.  The tree's build must be complete in stream
- * order (same stream, or synchronised).  Queries walk the levels with rank on
- * the bitmaps; node ranges are derived by rank, so the node table is not used.
+ * Batched queries over a built tree or matrix (Section 2 definitions), one
+ * result per query, enqueued on `stream`.  The build must be complete in
+ * stream order (same stream, or synchronised).  Queries walk the levels with
+ * rank on the bitmaps; node ranges are derived by rank, so the node table is
+ * not used.  On a matrix, a position moves to rank0 on a 0 bit and to
+ * d_zeros[l] + rank1 on a 1 bit (Section 7).
  *   wt_access: d_out[q] = S[d_i[q]]; UINT32_MAX when d_i[q] >= n.
  *   wt_rank:   d_out[q] = #{j <= d_i[q] : S[j] = d_c[q]} (inclusive);
  *              UINT64_MAX when d_i[q] >= n or d_c[q] >= sigma.

@@ -101,11 +101,11 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     if (nbins <= kBatchHistSmem && nbins * 4 <= (THREADS / 32) * stage_bytes<4>()) {
       for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
       __syncthreads();
-      prepass_tile<SB, THREADS, true>(a, tile, sIn, s_hist, sMisc, bad, nullptr, 0);
+      prepass_tile<SB, THREADS, kHistSmem>(a, tile, sIn, s_hist, sMisc, bad, nullptr, 0);
       for (uint32_t i = tid; i < nbins; i += THREADS)
         if (s_hist[i]) atomicAdd(&tr.hist[i], s_hist[i]);
     } else {
-      prepass_tile<SB, THREADS, false>(a, tile, sIn, s_hist, sMisc, bad, nullptr, 0);
+      prepass_tile<SB, THREADS, kHistGlobal>(a, tile, sIn, s_hist, sMisc, bad, nullptr, 0);
     }
     if (bad) latch_error(tr.err, WT_ERR_SYMBOL);
     return;
@@ -128,6 +128,8 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     a.log2T = 5 + (uint32_t)__ffs(THREADS) - 1;
     a.W = tr.W;
     a.tab = tr.tab + ((1u << level) - 1);
+    a.pshift = L - level;
+    a.matrix = 0;
     a.lo = lo;
     a.cin = tree_counts(tr, level);
     a.cout = tree_counts(tr, level + 1);

@@ -2,14 +2,15 @@
 //
 // One build (Shun, "Parallel Wavelet Tree Construction", Section 4, Fig. 1,
 // restated as global passes over each level's sequence T_l):
-//   pre-pass   reads S once: level-0 bits (bit L-1 of every symbol), level-0
-//              rank directory, the 2^L-bin symbol histogram, the range check.
+//   pre-pass   reads S once: the 2^L-bin symbol histogram, the range check,
+//              and the ones of level 0 (bit L-1) per tile.
 //   tables     node starts E[v] = #{S[j] < v} by an exclusive scan of the
 //              histogram; per level l and node prefix p the ones before the
 //              node, O_l[p], and the start of its 1-child.  These replace the
 //              per-node prefix-sum totals X_s and the node list A of Fig. 1.
-//   split(l)   l = 0..L-2: bits and directory of level l (l >= 1), the
-//              ones-before-tile prefix by single-pass decoupled look-back, and
+//   split(l)   l = 0..L-2: bits and directory of level l, the ones-before-
+//              tile prefix from the tile counts of the previous pass (each
+//              pass counts the next level's ones per destination tile), and
 //              the stable split of every node into its 0-child and 1-child
 //              ranges of T_{l+1} (Fig. 1's X_s + i - X[i] placement, with the
 //              prefix sum taken over the whole level instead of per node).
@@ -20,6 +21,11 @@
 // p = s >> (L-l), bit beta = bit (L-1-l) of s and R(j) = ones of level l
 // before j:  beta = 0 -> j - R(j) + O_l[p];  beta = 1 -> E_{l+1}[2p+1] +
 // R(j) - O_l[p].  The tables store {O_l[p], E_{l+1}[2p+1] - O_l[p]}.
+//
+// Wavelet matrix (Section 7): the same passes without histogram and tables;
+// every level is one node, so zeros go to j - R(j) and ones to Z_l + R(j),
+// Z_l = zeros of level l = n minus the level's ones, which the previous pass
+// (or the pre-pass, for level 0) has counted.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -141,14 +147,20 @@ int launch_prepass(Launcher &ln, const uint8_t *in, bool in_padded) {
   a.err = ln.err();
   const uint32_t nbins = 1u << t->L;
   ln.before(kPrepass);
-  if (nbins <= kHistSmemMaxBins) {
-    auto kern = k_prepass<SB, THREADS, true>;
+  if (t->shape == WT_SHAPE_MATRIX) {
+    auto kern = k_prepass<SB, THREADS, kHistNone>;
+    const size_t sm = prepass_smem_bytes<SB, THREADS>(0);
+    if (int rc = set_smem(kern, sm)) return rc;
+    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
+    kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
+  } else if (nbins <= kHistSmemMaxBins) {
+    auto kern = k_prepass<SB, THREADS, kHistSmem>;
     const size_t sm = prepass_smem_bytes<SB, THREADS>(nbins);
     if (int rc = set_smem(kern, sm)) return rc;
     const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
     kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
   } else {
-    auto kern = k_prepass<SB, THREADS, false>;
+    auto kern = k_prepass<SB, THREADS, kHistGlobal>;
     const size_t sm = prepass_smem_bytes<SB, THREADS>(0);
     if (int rc = set_smem(kern, sm)) return rc;
     const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
@@ -202,7 +214,10 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.NB = (uint32_t)t->NB;
   a.log2T = 5 + (uint32_t)__builtin_ctz(THREADS);
   a.W = t->W;
-  a.tab = t->d_tab + ((1u << level) - 1);
+  const bool matrix = t->shape == WT_SHAPE_MATRIX;
+  a.tab = matrix ? nullptr : t->d_tab + ((1u << level) - 1);
+  a.pshift = matrix ? t->L : t->L - level;
+  a.matrix = matrix ? 1 : 0;
   a.lo = ln.out(level);
   a.cin = ln.counts(level);
   a.cout = ln.counts(level + 1);
@@ -260,7 +275,7 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
   Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
   int rc;
   if ((rc = launch_prepass<SB, THREADS>(ln, seq, seq_padded))) return rc;
-  if ((rc = launch_tables(ln))) return rc;
+  if (t->shape == WT_SHAPE_TREE && (rc = launch_tables(ln))) return rc;
   if (t->L == 0) return WT_OK;
   const uint8_t *in = seq;
   bool padded = seq_padded;
@@ -317,8 +332,12 @@ uint32_t pick_threads(uint64_t n, uint32_t sb, int sms, uint32_t requested) {
 // ====================================================================== C ABI
 extern "C" {
 
-int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
-              wt_tree **out) {
+}  // extern "C"
+
+namespace {
+
+int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+                 uint32_t shape, wt_tree **out) {
   if (!out) return WT_ERR_ARG;
   *out = nullptr;
   if (!(symbol_bytes == 1 || symbol_bytes == 2 || symbol_bytes == 4)) return WT_ERR_ARG;
@@ -344,6 +363,7 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
   t->sigma = sigma;
   t->sb = symbol_bytes;
   t->L = L;
+  t->shape = shape;
   t->NB = (n + 511) / 512;
   t->W = 16 * t->NB;
   t->threads = pick_threads(n, symbol_bytes, t->sms, t->cfg.tile_threads);
@@ -357,13 +377,16 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
     return cuda_fail(e);
   };
   cudaError_t e;
-  const uint64_t nbins = 1ull << L;
+  const bool tree = shape == WT_SHAPE_TREE;
+  const uint64_t nbins = tree ? 1ull << L : 0;  // the matrix needs no histogram or node tables
   const size_t Lz = std::max<uint32_t>(L, 1);
   if ((e = cudaMalloc(&t->d_bits, std::max<size_t>(4, Lz * t->W * 4)))) return fail(e);
   if ((e = cudaMalloc(&t->d_rank, Lz * (t->NB + 1) * 8))) return fail(e);
   if ((e = cudaMalloc(&t->d_zeros, Lz * 8))) return fail(e);
-  if ((e = cudaMalloc(&t->d_node_start, (nbins + 1) * 8))) return fail(e);
-  if ((e = cudaMalloc(&t->d_tab, std::max<uint64_t>(1, nbins / 2) * sizeof(uint2)))) return fail(e);
+  if (tree) {
+    if ((e = cudaMalloc(&t->d_node_start, (nbins + 1) * 8))) return fail(e);
+    if ((e = cudaMalloc(&t->d_tab, std::max<uint64_t>(1, nbins / 2) * sizeof(uint2)))) return fail(e);
+  }
   t->counts_per_level = t->NT + (t->NT >> 6) + 1 + (t->NT >> 12) + 1;
   t->ctrl_words = kCtrlWords + nbins + (uint64_t)Lz * t->counts_per_level;
   if ((e = cudaMalloc(&t->d_ctrl, t->ctrl_words * 4))) return fail(e);
@@ -381,6 +404,20 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
   if ((e = cudaMemset(t->d_rank, 0, Lz * (t->NB + 1) * 8))) return fail(e);
   *out = t;
   return WT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+              wt_tree **out) {
+  return create_shape(n, sigma, symbol_bytes, cfg, WT_SHAPE_TREE, out);
+}
+
+int wt_matrix_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+                     wt_tree **out) {
+  return create_shape(n, sigma, symbol_bytes, cfg, WT_SHAPE_MATRIX, out);
 }
 
 int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
@@ -408,7 +445,7 @@ int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
   if (t->n == 0) {
     // nothing to scan: zero bits/directories are already in place; node
     // starts are all zero
-    WT_CUDA(cudaMemsetAsync(t->d_node_start, 0, (nbins + 1) * 8, st));
+    if (t->d_node_start) WT_CUDA(cudaMemsetAsync(t->d_node_start, 0, (nbins + 1) * 8, st));
     return WT_OK;
   }
   switch (t->sb) {
@@ -434,6 +471,18 @@ int wt_build_ex(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_b
 int wt_build(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes, void *stream,
              wt_tree **out) {
   return wt_build_ex(d_seq, n, sigma, symbol_bytes, nullptr, stream, out);
+}
+
+int wt_matrix_build(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
+                    const wt_config *cfg, void *stream, wt_tree **out) {
+  int rc = wt_matrix_create(n, sigma, symbol_bytes, cfg, out);
+  if (rc) return rc;
+  rc = wt_rebuild(*out, d_seq, stream);
+  if (rc) {
+    wt_free(*out);
+    *out = nullptr;
+  }
+  return rc;
 }
 
 int wt_sync(wt_tree *t) {
@@ -467,7 +516,7 @@ int wt_info(const wt_tree *t, wt_info_t *info) {
   info->sigma = t->sigma;
   info->symbol_bytes = t->sb;
   info->levels = t->L;
-  info->reserved = 0;
+  info->shape = t->shape;
   info->words_per_level = t->W;
   info->blocks = t->NB;
   info->d_bits = t->d_bits;
@@ -509,7 +558,8 @@ int wt_profile_read(wt_tree *t, float *ms, int32_t *kind, int32_t cap) {
 int wt_kernels_per_build(const wt_tree *t) {
   if (!t) return WT_ERR_ARG;
   if (t->n == 0) return 0;
-  int k = 2 + (tables_blocks(t->L) ? 1 : 0);  // pre-pass, histogram scan, tables
+  int k = 1;                                              // pre-pass
+  if (t->shape == WT_SHAPE_TREE) k += 1 + (tables_blocks(t->L) ? 1 : 0);  // histogram scan, tables
   if (t->L >= 1) k += (int)(t->L - 1) + 1;    // splits + last level
   return k;
 }

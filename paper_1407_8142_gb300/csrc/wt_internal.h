@@ -20,6 +20,7 @@ enum KernelKind : int32_t { kPrepass = 0, kHistScan = 1, kTables = 2, kSplit = 3
 struct wt_tree {
   uint64_t n = 0;
   uint32_t sigma = 0, sb = 0, L = 0;
+  uint32_t shape = WT_SHAPE_TREE;  // WT_SHAPE_TREE or WT_SHAPE_MATRIX
   uint64_t W = 0, NB = 0;
   uint32_t threads = 0;         // CTA size of the level passes
   uint64_t T = 0;               // symbols per tile
@@ -34,7 +35,7 @@ struct wt_tree {
   unsigned long long *d_node_start = nullptr;
   // scratch
   uint2 *d_tab = nullptr;       // per level l (heap offset 2^l - 1): {O_l[p], E_{l+1}[2p+1]-O_l[p]}
-  uint32_t *d_ctrl = nullptr;   // kCtrlWords control words followed by the 2^L histogram
+  uint32_t *d_ctrl = nullptr;   // kCtrlWords control words followed by the 2^L histogram (tree)
   uint32_t *d_hist = nullptr;
   uint32_t *d_counts = nullptr;   // per level: ones per tile, per 64 tiles, per 4096 tiles
   uint64_t counts_per_level = 0;

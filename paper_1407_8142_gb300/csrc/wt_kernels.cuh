@@ -189,6 +189,11 @@ constexpr uint32_t pipe_smem_bytes() {
 }
 
 // ------------------------------------------------------------------ pre-pass
+// Where the pre-pass keeps its symbol histogram: nowhere (the wavelet matrix
+// needs none), in shared-memory bins, or in global bins updated with
+// warp-aggregated atomics.
+enum HistMode : int { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2 };
+
 struct PrepassArgs {
   const uint8_t *in;  // S, 16-byte aligned
   int in_padded;
@@ -205,11 +210,10 @@ constexpr uint32_t prepass_smem_bytes(uint32_t hist_bins) {
   return pipe_smem_bytes<SB, THREADS>() + 4u * hist_bins + 64u;
 }
 
-// One pre-pass tile: symbol histogram (shared-memory bins when HIST_SMEM,
-// else warp-aggregated global atomics), range check (into `bad`) and the
-// level-0 ones of the tile.  Ends with a block barrier, after which thread 0
+// One pre-pass tile: symbol histogram (per HIST), range check (into `bad`)
+// and the level-0 ones of the tile.  Ends with a block barrier, after which thread 0
 // has stored ring_value to *ring_slot (if non-null).
-template <int SB, int THREADS, bool HIST_SMEM>
+template <int SB, int THREADS, int HIST>
 __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile, const uint8_t *sIn,
                                            uint32_t *s_hist, uint32_t *s_wt, uint32_t &bad,
                                            uint32_t *ring_slot, uint32_t ring_value) {
@@ -223,12 +227,21 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
   uint32_t u[8 * SB];
   load_from_smem<SB, THREADS>(sIn, my0, u);
   const uint32_t word = a.L ? pack_bits<SB>(u, a.L - 1) & valid_mask(my0, nv) : 0u;
-  if (__all_sync(0xFFFFFFFFu, my0 + 32 <= nv)) {  // warp-uniform: the loop uses warp collectives
+  if (HIST == kHistNone) {
+    // range check only, and only when the storage type can exceed sigma
+    if (a.sigma < (SB == 4 ? 0xFFFFFFFFu : (1u << (8 * SB)))) {
+      uint32_t mx = 0;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q)
+        if (my0 + q < nv) mx = max(mx, symbol_at<SB>(u, q));
+      bad |= (uint32_t)(mx >= a.sigma);
+    }
+  } else if (__all_sync(0xFFFFFFFFu, my0 + 32 <= nv)) {  // warp-uniform: the loop uses warp collectives
 #pragma unroll 8
     for (int q = 0; q < 32; ++q) {
       const uint32_t s = symbol_at<SB>(u, q);
       bad |= (uint32_t)(s >= a.sigma);
-      if (HIST_SMEM) {
+      if (HIST == kHistSmem) {
         atomicAdd(&s_hist[s & lmask], 1u);
       } else {
         const uint32_t v = s & lmask;
@@ -241,7 +254,7 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
       const bool valid = my0 + q < nv;
       const uint32_t s = symbol_at<SB>(u, q);
       if (valid) bad |= (uint32_t)(s >= a.sigma);
-      if (HIST_SMEM) {
+      if (HIST == kHistSmem) {
         if (valid) atomicAdd(&s_hist[s & lmask], 1u);
       } else {
         const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
@@ -270,9 +283,9 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
   __syncthreads();
 }
 
-// Reads S once: the 2^L-bin histogram (node sizes of every level), the range
-// check, and the level-0 ones of every tile.
-template <int SB, int THREADS, bool HIST_SMEM>
+// Reads S once: the 2^L-bin histogram (node sizes of every level; not for
+// the wavelet matrix), the range check, and the level-0 ones of every tile.
+template <int SB, int THREADS, int HIST>
 __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
   constexpr uint32_t T = 32 * THREADS;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -281,7 +294,7 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
   pipe.sIn0 = smem;
   pipe.sIn1 = smem + pipe.TB;
   uint32_t *const s_hist = reinterpret_cast<uint32_t *>(smem + 2 * pipe.TB);
-  uint64_t *const bar = reinterpret_cast<uint64_t *>(s_hist + (HIST_SMEM ? ((nbins + 1) & ~1u) : 0));
+  uint64_t *const bar = reinterpret_cast<uint64_t *>(s_hist + (HIST == kHistSmem ? ((nbins + 1) & ~1u) : 0));
   pipe.bar = bar;
   pipe.ring = reinterpret_cast<uint32_t *>(bar + 2);
   uint32_t *const s_wt = pipe.ring + 4;  // ones per warp
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
   pipe.ticket = a.ticket;
   const uint32_t tid = threadIdx.x;
   uint32_t bad = 0;
-  if (HIST_SMEM)
+  if (HIST == kHistSmem)
     for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
   if (tid == 0) pipe.prologue();
   __syncthreads();
@@ -313,11 +326,11 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
     const uint32_t nv = (uint32_t)umin64(T, a.n - start);
     uint8_t *const sIn = pipe.data(it);
     if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
-    prepass_tile<SB, THREADS, HIST_SMEM>(a, tile, sIn, s_hist, s_wt, bad,
+    prepass_tile<SB, THREADS, HIST>(a, tile, sIn, s_hist, s_wt, bad,
                                          tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
   }
   if (bad) latch_error(a.err, WT_ERR_SYMBOL);
-  if (HIST_SMEM) {
+  if (HIST == kHistSmem) {
     __syncthreads();
     for (uint32_t i = tid; i < nbins; i += THREADS)
       if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
@@ -430,6 +443,8 @@ struct SplitArgs {
   uint32_t n, L, level, NT, NB, log2T;
   uint64_t W;
   const uint2 *tab;    // this level's {O_l[p], E_{l+1}[2p+1] - O_l[p]}
+  uint32_t pshift;     // node prefix = symbol >> pshift (L - level; L for the matrix)
+  int matrix;          // wavelet matrix: one node, table {0, zeros of level l}
   LevelOut lo;
   TileCounts cin;      // ones of level l per tile of T_l
   TileCounts cout;     // ones of level l+1 per tile of T_{l+1} (accumulated here)
@@ -564,7 +579,7 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t k = a.L - 1 - a.level;   // bit of this level
   const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
-  const uint32_t pshift = a.L - a.level;  // node prefix = symbol >> pshift
+  const uint32_t pshift = a.pshift;       // node prefix = symbol >> pshift
   const uint32_t lmask = (1u << a.L) - 1u;
   uint8_t *const stage = sm.stage + warp * stage_bytes<SB>();
   Sym *const stageS = reinterpret_cast<Sym *>(stage);
@@ -775,12 +790,23 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_sp
   pipe.ticket = a.ticket;
 
   const uint32_t tid = threadIdx.x;
-  const uint32_t nodes = 1u << a.level;
+  const uint32_t nodes = 1u << (a.L - a.pshift);
   const bool tab_smem = nodes <= kTabSmem;
   const uint2 *const tab = tab_smem ? sTab : a.tab;
 
-  if (tab_smem)
+  if (a.matrix) {
+    // Wavelet matrix (Section 7): the whole level is one node; its ones go
+    // after all zeros of the level, which are n minus the level's ones,
+    // summed from the top tier of the level's tile counts.
+    if (tid < 32) {
+      uint32_t ones = 0;
+      for (uint32_t i = tid; i <= (a.NT - 1) >> 12; i += 32) ones += __ldcg(&a.cin.c2[i]);
+      ones = __reduce_add_sync(0xFFFFFFFFu, ones);
+      if (tid == 0) sTab[0] = make_uint2(0u, a.n - ones);
+    }
+  } else if (tab_smem) {
     for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
+  }
   if (tid < 4) sCnt[tid] = 0;
   if (tid == 0) pipe.prologue();
   __syncthreads();

@@ -1,8 +1,10 @@
-// Batched access / rank / select over a built levelwise wavelet tree, one
-// thread per query (validation path).  Definitions from Section 2 of the
-// paper; the walks derive node ranges by rank on the level bitmaps (the
-// child of [s, e) on level l is [s, s+z) or [s+z, e) on level l+1, z the
-// zeros of B_l[s, e)), so no node table is needed.
+// Batched access / rank / select over a built levelwise wavelet tree or
+// wavelet matrix, one thread per query (validation path).  Definitions from
+// Section 2 of the paper.  Tree walks derive node ranges by rank on the
+// level bitmaps (the child of [s, e) on level l is [s, s+z) or [s+z, e) on
+// level l+1, z the zeros of B_l[s, e)), so no node table is needed.  Matrix
+// walks (Section 7) move a position to rank0(i) on a 0 bit and to
+// Z_l + rank1(i) on a 1 bit, Z_l the zeros of level l.
 #include <cstdint>
 
 #include "wt_dev.cuh"
@@ -15,6 +17,7 @@ namespace {
 struct QTree {
   const uint32_t *bits;
   const unsigned long long *rank;
+  const unsigned long long *zeros;
   uint64_t W, NB;
   uint32_t n, L, sigma;
 };
@@ -159,10 +162,93 @@ __global__ void k_select(QTree t, const uint32_t *cs, const uint64_t *ks, uint64
   }
 }
 
+// ----------------------------------------------------------- wavelet matrix
+__global__ void k_maccess(QTree t, const uint64_t *idx, uint64_t m, uint32_t *out) {
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i0 = idx[q];
+    if (i0 >= t.n) {
+      out[q] = 0xFFFFFFFFu;
+      continue;
+    }
+    uint32_t i = (uint32_t)i0, code = 0;
+    for (uint32_t l = 0; l < t.L; ++l) {
+      const uint32_t bit = bit_at(t, l, i);
+      const uint32_t r1 = rank1(t, l, i);
+      i = bit ? (uint32_t)t.zeros[l] + r1 : i - r1;
+      code = 2 * code + bit;
+    }
+    out[q] = code;
+  }
+}
+
+__global__ void k_mrank(QTree t, const uint32_t *cs, const uint64_t *idx, uint64_t m,
+                        unsigned long long *out) {
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i0 = idx[q];
+    const uint32_t c = cs[q];
+    if (i0 >= t.n || c >= t.sigma) {
+      out[q] = ~0ull;
+      continue;
+    }
+    // [s, e) holds the symbols of S[0..i] that share c's top l bits
+    uint32_t s = 0, e = (uint32_t)i0 + 1;
+    for (uint32_t l = 0; l < t.L; ++l) {
+      const uint32_t rs = rank1(t, l, s), re = rank1(t, l, e);
+      if ((c >> (t.L - 1 - l)) & 1u) {
+        const uint32_t z = (uint32_t)t.zeros[l];
+        s = z + rs;
+        e = z + re;
+      } else {
+        s -= rs;
+        e -= re;
+      }
+    }
+    out[q] = e - s;
+  }
+}
+
+__global__ void k_mselect(QTree t, const uint32_t *cs, const uint64_t *ks, uint64_t m,
+                          unsigned long long *out) {
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ks[q];
+    const uint32_t c = cs[q];
+    if (k == 0 || c >= t.sigma) {
+      out[q] = ~0ull;
+      continue;
+    }
+    uint32_t s = 0, e = t.n;  // all occurrences of c's top l bits
+    for (uint32_t l = 0; l < t.L; ++l) {
+      const uint32_t rs = rank1(t, l, s), re = rank1(t, l, e);
+      if ((c >> (t.L - 1 - l)) & 1u) {
+        const uint32_t z = (uint32_t)t.zeros[l];
+        s = z + rs;
+        e = z + re;
+      } else {
+        s -= rs;
+        e -= re;
+      }
+    }
+    if (k > (uint64_t)(e - s)) {
+      out[q] = ~0ull;
+      continue;
+    }
+    uint32_t pos = s + (uint32_t)k - 1;  // in the order after the last level
+    for (int l = (int)t.L - 1; l >= 0; --l) {
+      if ((c >> (t.L - 1 - l)) & 1u) pos = select_bit(t, l, pos - (uint32_t)t.zeros[l], 1);
+      else pos = select_bit(t, l, pos, 0);
+    }
+    out[q] = pos;
+  }
+}
+
 QTree qtree(const wt_tree *t) {
   QTree q;
   q.bits = t->d_bits;
   q.rank = t->d_rank;
+  q.zeros = t->d_zeros;
   q.W = t->W;
   q.NB = t->NB;
   q.n = (uint32_t)t->n;
@@ -189,7 +275,8 @@ int wt_access(const wt_tree *t, const uint64_t *d_i, uint64_t m, uint32_t *d_out
   if (!t || (m && (!d_i || !d_out))) return WT_ERR_ARG;
   if (t->sticky_error) return t->sticky_error;
   if (!m) return WT_OK;
-  k_access<<<grid_for(m), 256, 0, static_cast<cudaStream_t>(stream)>>>(qtree(t), d_i, m, d_out);
+  auto kern = t->shape == WT_SHAPE_MATRIX ? k_maccess : k_access;
+  kern<<<grid_for(m), 256, 0, static_cast<cudaStream_t>(stream)>>>(qtree(t), d_i, m, d_out);
   return check_launch();
 }
 
@@ -198,7 +285,8 @@ int wt_rank(const wt_tree *t, const uint32_t *d_c, const uint64_t *d_i, uint64_t
   if (!t || (m && (!d_c || !d_i || !d_out))) return WT_ERR_ARG;
   if (t->sticky_error) return t->sticky_error;
   if (!m) return WT_OK;
-  k_rank<<<grid_for(m), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+  auto kern = t->shape == WT_SHAPE_MATRIX ? k_mrank : k_rank;
+  kern<<<grid_for(m), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       qtree(t), d_c, d_i, m, reinterpret_cast<unsigned long long *>(d_out));
   return check_launch();
 }
@@ -208,7 +296,8 @@ int wt_select(const wt_tree *t, const uint32_t *d_c, const uint64_t *d_k, uint64
   if (!t || (m && (!d_c || !d_k || !d_out))) return WT_ERR_ARG;
   if (t->sticky_error) return t->sticky_error;
   if (!m) return WT_OK;
-  k_select<<<grid_for(m), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+  auto kern = t->shape == WT_SHAPE_MATRIX ? k_mselect : k_select;
+  kern<<<grid_for(m), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       qtree(t), d_c, d_k, m, reinterpret_cast<unsigned long long *>(d_out));
   return check_launch();
 }

@@ -27,6 +27,8 @@ ERROR_NAMES = {WT_ERR_ARG: "WT_ERR_ARG", WT_ERR_OOM: "WT_ERR_OOM", WT_ERR_CUDA: 
                WT_ERR_SYMBOL: "WT_ERR_SYMBOL", WT_ERR_TIMEOUT: "WT_ERR_TIMEOUT"}
 
 KERNEL_KINDS = {0: "prepass", 1: "hist_scan", 2: "tables", 3: "split", 4: "leaf"}
+WT_SHAPE_TREE = 0
+WT_SHAPE_MATRIX = 1
 
 
 class WTError(RuntimeError):
@@ -43,7 +45,7 @@ class Config(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("sigma", ctypes.c_uint32),
                 ("symbol_bytes", ctypes.c_uint32), ("levels", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("words_per_level", ctypes.c_uint64),
+                ("shape", ctypes.c_uint32), ("words_per_level", ctypes.c_uint64),
                 ("blocks", ctypes.c_uint64), ("d_bits", ctypes.c_void_p),
                 ("d_rank", ctypes.c_void_p), ("d_zeros", ctypes.c_void_p),
                 ("d_node_start", ctypes.c_void_p)]
@@ -63,6 +65,8 @@ SIGNATURES = {
     "wt_build": (ctypes.c_int, [P, U64, U32, U32, P, ctypes.POINTER(P)]),
     "wt_build_ex": (ctypes.c_int, [P, U64, U32, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
     "wt_build_host": (ctypes.c_int, [P, P, P, P, P]),
+    "wt_matrix_create": (ctypes.c_int, [U64, U32, U32, ctypes.POINTER(Config), ctypes.POINTER(P)]),
+    "wt_matrix_build": (ctypes.c_int, [P, U64, U32, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
     "wt_sync": (ctypes.c_int, [P]),
     "wt_info": (ctypes.c_int, [P, ctypes.POINTER(Info)]),
     "wt_access": (ctypes.c_int, [P, P, U64, P, P]),
@@ -175,6 +179,21 @@ def wt_build(d_seq: int, n: int, sigma: int, symbol_bytes: int, stream=None,
     return out.value
 
 
+def wt_matrix_create(n: int, sigma: int, symbol_bytes: int, cfg: Config | None = None) -> int:
+    out = P()
+    _check(load().wt_matrix_create(n, sigma, symbol_bytes, ctypes.byref(cfg) if cfg else None,
+                                   ctypes.byref(out)), "wt_matrix_create")
+    return out.value
+
+
+def wt_matrix_build(d_seq: int, n: int, sigma: int, symbol_bytes: int, stream=None,
+                    cfg: Config | None = None) -> int:
+    out = P()
+    _check(load().wt_matrix_build(d_seq, n, sigma, symbol_bytes, ctypes.byref(cfg) if cfg else None,
+                                  _stream_ptr(stream), ctypes.byref(out)), "wt_matrix_build")
+    return out.value
+
+
 def wt_build_host(tree: int, h_seq: int, h_bits: int | None, h_rank: int | None,
                   stream=None) -> int:
     return load().wt_build_host(tree, h_seq, h_bits, h_rank, _stream_ptr(stream))
@@ -240,11 +259,13 @@ def _torch_symbols(seq):
 class WaveletTree:
     """A device-resident levelwise wavelet tree (owns a wt_tree)."""
 
+    _create = staticmethod(wt_create)
+
     def __init__(self, n: int, sigma: int, symbol_bytes: int, tile_threads: int = 0,
                  ctas_per_sm: int = 0, spin_limit: int = 0, debug_skip_publish: int = 0):
         self.cfg = Config(tile_threads, ctas_per_sm, spin_limit, debug_skip_publish)
         self.n, self.sigma, self.symbol_bytes = n, sigma, symbol_bytes
-        self.handle = wt_create(n, sigma, symbol_bytes, self.cfg)
+        self.handle = type(self)._create(n, sigma, symbol_bytes, self.cfg)
         self._keep = None
 
     # construction
@@ -289,7 +310,8 @@ class WaveletTree:
         out["bits"] = d2h(np.empty((L, W), dtype=np.uint32), inf.d_bits)
         out["rank"] = d2h(np.empty((L, NB + 1), dtype=np.uint64), inf.d_rank)
         out["zeros"] = d2h(np.empty(L, dtype=np.uint64), inf.d_zeros)
-        out["node_start"] = d2h(np.empty((1 << L) + 1, dtype=np.uint64), inf.d_node_start)
+        if inf.d_node_start:
+            out["node_start"] = d2h(np.empty((1 << L) + 1, dtype=np.uint64), inf.d_node_start)
         return out
 
     # queries
@@ -340,6 +362,24 @@ class WaveletTree:
             self.free()
         except Exception:
             pass
+
+
+class WaveletMatrix(WaveletTree):
+    """A device-resident wavelet matrix (Section 7; owns a wt_tree of shape
+    WT_SHAPE_MATRIX).  Same outputs and queries as WaveletTree, without node
+    starts."""
+
+    _create = staticmethod(wt_matrix_create)
+
+
+def build_matrix(seq, sigma: int, **cfg) -> WaveletMatrix:
+    """Create a wavelet matrix for `seq` (numpy array or CUDA tensor) and
+    enqueue its build."""
+    if isinstance(seq, np.ndarray):
+        n, b = seq.size, seq.dtype.itemsize
+    else:
+        n, b = seq.numel(), seq.element_size()
+    return WaveletMatrix(n, sigma, b, **cfg).build(seq)
 
 
 def build_tree(seq, sigma: int, **cfg) -> WaveletTree:
