@@ -315,6 +315,7 @@ def main_ours(args):
     split_bytes = split_ms = 0.0
     split_launches = 0
     level = 0
+    per_level = [[0, 0.0] for _ in range(max(L - 1, 0))]
     for kind, ms in prof:
         if kind == "prepass":
             level = 0
@@ -325,6 +326,9 @@ def main_ours(args):
             split_bytes += algorithmic_bytes("split", level, n, sb, L)
             split_ms += ms
             split_launches += 1
+            if level < len(per_level):
+                per_level[level][0] += 1
+                per_level[level][1] += ms
             level += 1
     total_kernel_ms = sum(v[1] for v in per_kind.values())
     peak, peak_kind = measured_hbm_peak()
@@ -343,6 +347,7 @@ def main_ours(args):
                 "algorithmic_bytes_per_launch": split_bytes / max(split_launches, 1),
                 "mean_launch_ms": split_ms / max(split_launches, 1),
                 "time_share": round(split_ms / total_kernel_ms, 4) if total_kernel_ms else None,
+                "split_ms_per_level": [round(t / c, 4) if c else None for c, t in per_level],
                 "whole_build_gbs": round(build_bytes / (ms_step * 1e-3) / 1e9, 1)}
 
     # end to end through the public host-buffer entry point

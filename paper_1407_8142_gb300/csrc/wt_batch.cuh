@@ -105,7 +105,7 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
       for (uint32_t i = tid; i < nbins; i += THREADS)
         if (s_hist[i]) atomicAdd(&tr.hist[i], s_hist[i]);
     } else {
-      prepass_tile<SB, THREADS, kHistGlobal>(a, tile, sIn, s_hist, sMisc, bad, nullptr, 0);
+      prepass_tile<SB, THREADS, kHistGlobal>(a, tile, sIn, nullptr, sMisc, bad, nullptr, 0);
     }
     if (bad) latch_error(tr.err, WT_ERR_SYMBOL);
     return;

@@ -130,6 +130,17 @@ int set_smem(K kern, size_t bytes) {
   return WT_OK;
 }
 
+// Persistent launch: as many CTAs as fit on the GPU (capped by ctas_per_sm),
+// never more than there are tiles.
+template <typename K, typename A>
+int launch_persistent(Launcher &ln, K kern, int threads, size_t smem, const A &args) {
+  wt_tree *t = ln.t;
+  if (int rc = set_smem(kern, smem)) return rc;
+  const int grid = std::min<int>((int)t->NT, occupancy(kern, threads, smem, t->sms, t->cfg.ctas_per_sm));
+  kern<<<std::max(grid, 1), threads, smem, ln.st>>>(args);
+  return WT_OK;
+}
+
 template <int SB, int THREADS>
 int launch_prepass(Launcher &ln, const uint8_t *in, bool in_padded) {
   wt_tree *t = ln.t;
@@ -147,25 +158,19 @@ int launch_prepass(Launcher &ln, const uint8_t *in, bool in_padded) {
   a.err = ln.err();
   const uint32_t nbins = 1u << t->L;
   ln.before(kPrepass);
-  if (t->shape == WT_SHAPE_MATRIX) {
-    auto kern = k_prepass<SB, THREADS, kHistNone>;
-    const size_t sm = prepass_smem_bytes<SB, THREADS>(0);
-    if (int rc = set_smem(kern, sm)) return rc;
-    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
-    kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
-  } else if (nbins <= kHistSmemMaxBins) {
-    auto kern = k_prepass<SB, THREADS, kHistSmem>;
-    const size_t sm = prepass_smem_bytes<SB, THREADS>(nbins);
-    if (int rc = set_smem(kern, sm)) return rc;
-    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
-    kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
-  } else {
-    auto kern = k_prepass<SB, THREADS, kHistGlobal>;
-    const size_t sm = prepass_smem_bytes<SB, THREADS>(0);
-    if (int rc = set_smem(kern, sm)) return rc;
-    const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
-    kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
-  }
+  int rc;
+  if (t->shape == WT_SHAPE_MATRIX)
+    rc = launch_persistent(ln, k_prepass<SB, THREADS, kHistNone>, THREADS, prepass_smem_bytes<SB, THREADS>(0), a);
+  else if (nbins <= kHistLanesMaxBins)
+    rc = launch_persistent(ln, k_prepass<SB, THREADS, kHistLanes>, THREADS,
+                           prepass_smem_bytes<SB, THREADS>(hist_smem_words(kHistLanes, nbins)), a);
+  else if (nbins <= kHistSmemMaxBins)
+    rc = launch_persistent(ln, k_prepass<SB, THREADS, kHistSmem>, THREADS,
+                           prepass_smem_bytes<SB, THREADS>(hist_smem_words(kHistSmem, nbins)), a);
+  else
+    rc = launch_persistent(ln, k_prepass<SB, THREADS, kHistGlobal>, THREADS,
+                           prepass_smem_bytes<SB, THREADS>(hist_smem_words(kHistGlobal, nbins)), a);
+  if (rc) return rc;
   ln.after();
   ++ln.pass;
   WT_CUDA(cudaGetLastError());

@@ -213,6 +213,13 @@ __device__ __forceinline__ const uint32_t *prefix_term(const TileCounts &c, uint
   return c.c0 + ((t >> 6) << 6) + j;
 }
 
+// Total of a level's counts over all NT tiles, from the top tier (one warp).
+__device__ __forceinline__ uint32_t counts_total_warp(const TileCounts &c, uint32_t NT) {
+  uint32_t s = 0;
+  for (uint32_t i = threadIdx.x & 31; i <= (NT - 1) >> 12; i += 32) s += __ldcg(&c.c2[i]);
+  return __reduce_add_sync(0xFFFFFFFFu, s);
+}
+
 // This thread's share of the exclusive prefix of tile t (sum over threads).
 template <int THREADS>
 __device__ __forceinline__ uint32_t prefix_share(const TileCounts &c, uint32_t t) {

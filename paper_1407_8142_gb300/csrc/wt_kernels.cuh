@@ -183,6 +183,34 @@ __device__ __forceinline__ void load_from_smem(const uint8_t *sIn, uint32_t my0,
   }
 }
 
+// Bit k of this thread's 32 symbols (positions my0..my0+31 of the tile held
+// in sIn) as one word, symbol q -> bit q.  One-byte symbols: two 16-byte
+// loads and SWAR packing per thread.  Wider symbols: the warp reads its
+// 32 x 32 symbols row by row (lane i takes symbol 32c + i: consecutive
+// addresses, no bank conflict) and the ballot of row c is the word of the
+// thread that owns it; per-thread 16-byte loads of 64 or 128 consecutive
+// bytes would serialise 4 or 8 ways on the shared-memory banks.
+// Called by all threads of the warp.
+template <int SB, int THREADS>
+__device__ __forceinline__ uint32_t tile_word(const uint8_t *sIn, uint32_t my0, uint32_t k) {
+  if (SB == 1) {
+    uint32_t u[8];
+    load_from_smem<1, THREADS>(sIn, my0, u);
+    return pack_bits<1>(u, k);
+  } else {
+    using Sym = typename SymT<SB>::type;
+    const uint32_t lane = threadIdx.x & 31;
+    const Sym *rows = reinterpret_cast<const Sym *>(sIn) + (my0 - 32 * lane);
+    uint32_t word = 0;
+#pragma unroll 8
+    for (uint32_t c = 0; c < 32; ++c) {
+      const uint32_t b = __ballot_sync(0xFFFFFFFFu, ((uint32_t)rows[32 * c + lane] >> k) & 1u);
+      word = lane == c ? b : word;
+    }
+    return word;
+  }
+}
+
 template <int SB, int THREADS>
 constexpr uint32_t pipe_smem_bytes() {
   return 2u * 32u * THREADS * SB;
@@ -190,9 +218,45 @@ constexpr uint32_t pipe_smem_bytes() {
 
 // ------------------------------------------------------------------ pre-pass
 // Where the pre-pass keeps its symbol histogram: nowhere (the wavelet matrix
-// needs none), in shared-memory bins, or in global bins updated with
-// warp-aggregated atomics.
-enum HistMode : int { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2 };
+// needs none), in shared-memory bins, in global bins updated with
+// warp-aggregated atomics, or (few bins) in shared memory with one copy of
+// every bin per lane: bin v of lane i at v * 32 + i, so the 32 updates of a
+// warp row always fall in 32 distinct banks (the copies are summed once per
+// CTA, each thread reading its bin's copies in a rotated order).
+enum HistMode : int { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2, kHistLanes = 3 };
+constexpr uint32_t kHistLanesMaxBins = 256;
+constexpr uint32_t kHotSlots = 1024;  // per-CTA table of hot bins for kHistGlobal
+constexpr uint32_t kHotEmpty = 0xFFFFFFFFu;
+
+__host__ __device__ constexpr uint32_t hist_smem_words(int mode, uint32_t nbins) {
+  return mode == kHistSmem ? ((nbins + 1) & ~1u)
+         : mode == kHistLanes ? nbins * 32
+         : mode == kHistGlobal ? 2u * kHotSlots : 0u;
+}
+
+// Add c occurrences of bin v to a global histogram (one lane).  A bin that
+// occurs more than once among a warp's 32 symbols of one step is likely hot
+// (skewed inputs), and global atomics on one hot word serialise across the
+// whole GPU: such bins are counted in `hot`, a per-CTA open-addressed table
+// in shared memory (kHotSlots tags, then kHotSlots counts; a slot, once
+// claimed, keeps its bin), which the caller flushes once.  Other bins, and
+// hot bins that find no slot within four probes, go to global memory.
+__device__ __forceinline__ void hist_add(uint32_t *ghist, uint32_t *hot, uint32_t v, uint32_t c) {
+  if (hot && c > 1) {
+    uint32_t slot = v & (kHotSlots - 1);
+#pragma unroll 1
+    for (int probe = 0; probe < 4; ++probe) {
+      uint32_t t = *reinterpret_cast<volatile uint32_t *>(&hot[slot]);
+      if (t == kHotEmpty) t = atomicCAS(&hot[slot], kHotEmpty, v);
+      if (t == kHotEmpty || t == v) {
+        atomicAdd(&hot[kHotSlots + slot], c);
+        return;
+      }
+      slot = (slot + 1) & (kHotSlots - 1);
+    }
+  }
+  atomicAdd(&ghist[v], c);
+}
 
 struct PrepassArgs {
   const uint8_t *in;  // S, 16-byte aligned
@@ -206,8 +270,8 @@ struct PrepassArgs {
 };
 
 template <int SB, int THREADS>
-constexpr uint32_t prepass_smem_bytes(uint32_t hist_bins) {
-  return pipe_smem_bytes<SB, THREADS>() + 4u * hist_bins + 64u;
+constexpr uint32_t prepass_smem_bytes(uint32_t hist_words) {
+  return pipe_smem_bytes<SB, THREADS>() + 4u * hist_words + 64u;
 }
 
 // One pre-pass tile: symbol histogram (per HIST), range check (into `bad`)
@@ -224,44 +288,53 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
   const uint64_t start = (uint64_t)tile * T;
   const uint32_t nv = (uint32_t)umin64(T, a.n - start);
   const uint32_t my0 = 32 * tid;
-  uint32_t u[8 * SB];
-  load_from_smem<SB, THREADS>(sIn, my0, u);
-  const uint32_t word = a.L ? pack_bits<SB>(u, a.L - 1) & valid_mask(my0, nv) : 0u;
+  const uint32_t word = a.L ? tile_word<SB, THREADS>(sIn, my0, a.L - 1) & valid_mask(my0, nv) : 0u;
+  // The warp walks its 1024 symbols row by row: lane i takes symbol 32c + i
+  // of row c (consecutive shared-memory addresses, and the symbols of a row
+  // are what the warp-wide aggregation below sees together).
+  using Sym = typename SymT<SB>::type;
+  const Sym *rows = reinterpret_cast<const Sym *>(sIn) + 1024 * warp;
+  const uint32_t seg = 1024 * warp;
+  const uint32_t nvw = nv > seg ? min(nv - seg, 1024u) : 0u;  // warp-uniform
   if (HIST == kHistNone) {
     // range check only, and only when the storage type can exceed sigma
     if (a.sigma < (SB == 4 ? 0xFFFFFFFFu : (1u << (8 * SB)))) {
       uint32_t mx = 0;
 #pragma unroll 8
-      for (int q = 0; q < 32; ++q)
-        if (my0 + q < nv) mx = max(mx, symbol_at<SB>(u, q));
+      for (uint32_t c = 0; c < 32; ++c)
+        if (32 * c + lane < nvw) mx = max(mx, (uint32_t)rows[32 * c + lane]);
       bad |= (uint32_t)(mx >= a.sigma);
     }
-  } else if (__all_sync(0xFFFFFFFFu, my0 + 32 <= nv)) {  // warp-uniform: the loop uses warp collectives
-#pragma unroll 8
-    for (int q = 0; q < 32; ++q) {
-      const uint32_t s = symbol_at<SB>(u, q);
+  } else if (nvw == 1024) {
+#pragma unroll 4
+    for (uint32_t c = 0; c < 32; ++c) {
+      const uint32_t s = rows[32 * c + lane];
       bad |= (uint32_t)(s >= a.sigma);
-      if (HIST == kHistSmem) {
-        atomicAdd(&s_hist[s & lmask], 1u);
+      const uint32_t v = s & lmask;
+      if (HIST == kHistLanes) {
+        atomicAdd(&s_hist[v * 32 + lane], 1u);
+      } else if (HIST == kHistSmem) {
+        atomicAdd(&s_hist[v], 1u);
       } else {
-        const uint32_t v = s & lmask;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, v);
-        if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
+        if (lane == (uint32_t)(__ffs(peers) - 1)) hist_add(a.hist, s_hist, v, (uint32_t)__popc(peers));
       }
     }
   } else {
-    for (int q = 0; q < 32; ++q) {
-      const bool valid = my0 + q < nv;
-      const uint32_t s = symbol_at<SB>(u, q);
-      if (valid) bad |= (uint32_t)(s >= a.sigma);
-      if (HIST == kHistSmem) {
-        if (valid) atomicAdd(&s_hist[s & lmask], 1u);
+    for (uint32_t c = 0; c < 32; ++c) {
+      const bool valid = 32 * c + lane < nvw;
+      const uint32_t s = valid ? (uint32_t)rows[32 * c + lane] : 0u;
+      bad |= (uint32_t)(s >= a.sigma);
+      const uint32_t v = s & lmask;
+      if (HIST == kHistLanes) {
+        if (valid) atomicAdd(&s_hist[v * 32 + lane], 1u);
+      } else if (HIST == kHistSmem) {
+        if (valid) atomicAdd(&s_hist[v], 1u);
       } else {
         const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
         if (valid) {
-          const uint32_t v = s & lmask;
           const uint32_t peers = __match_any_sync(am, v);
-          if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&a.hist[v], (uint32_t)__popc(peers));
+          if (lane == (uint32_t)(__ffs(peers) - 1)) hist_add(a.hist, s_hist, v, (uint32_t)__popc(peers));
         }
       }
     }
@@ -294,7 +367,7 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
   pipe.sIn0 = smem;
   pipe.sIn1 = smem + pipe.TB;
   uint32_t *const s_hist = reinterpret_cast<uint32_t *>(smem + 2 * pipe.TB);
-  uint64_t *const bar = reinterpret_cast<uint64_t *>(s_hist + (HIST == kHistSmem ? ((nbins + 1) & ~1u) : 0));
+  uint64_t *const bar = reinterpret_cast<uint64_t *>(s_hist + hist_smem_words(HIST, nbins));
   pipe.bar = bar;
   pipe.ring = reinterpret_cast<uint32_t *>(bar + 2);
   uint32_t *const s_wt = pipe.ring + 4;  // ones per warp
@@ -305,8 +378,8 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
   pipe.ticket = a.ticket;
   const uint32_t tid = threadIdx.x;
   uint32_t bad = 0;
-  if (HIST == kHistSmem)
-    for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
+  for (uint32_t i = tid; i < hist_smem_words(HIST, nbins); i += THREADS)
+    s_hist[i] = (HIST == kHistGlobal && i < kHotSlots) ? kHotEmpty : 0u;
   if (tid == 0) pipe.prologue();
   __syncthreads();
 
@@ -334,6 +407,18 @@ __global__ void __launch_bounds__(THREADS) k_prepass(PrepassArgs a) {
     __syncthreads();
     for (uint32_t i = tid; i < nbins; i += THREADS)
       if (s_hist[i]) atomicAdd(&a.hist[i], s_hist[i]);
+  } else if (HIST == kHistGlobal) {
+    __syncthreads();
+    for (uint32_t i = tid; i < kHotSlots; i += THREADS)
+      if (s_hist[i] != kHotEmpty && s_hist[kHotSlots + i]) atomicAdd(&a.hist[s_hist[i]], s_hist[kHotSlots + i]);
+  } else if (HIST == kHistLanes) {
+    __syncthreads();
+    for (uint32_t i = tid; i < nbins; i += THREADS) {
+      uint32_t c = 0;
+#pragma unroll 8
+      for (uint32_t r = 0; r < 32; ++r) c += s_hist[i * 32 + ((r + i) & 31u)];
+      if (c) atomicAdd(&a.hist[i], c);
+    }
   }
 }
 
@@ -367,10 +452,8 @@ __device__ __forceinline__ void leaf_tile(const LeafArgs &a, uint32_t tile, cons
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t start = (uint64_t)tile * T;
   const uint32_t nv = (uint32_t)umin64(T, a.n - start);
-    const uint32_t my0 = 32 * tid;
-  uint32_t u[8 * SB];
-  load_from_smem<SB, THREADS>(sIn, my0, u);
-  const uint32_t word = pack_bits<SB>(u, 0) & valid_mask(my0, nv);
+  const uint32_t my0 = 32 * tid;
+  const uint32_t word = tile_word<SB, THREADS>(sIn, my0, 0) & valid_mask(my0, nv);
   const uint32_t pc = __popc(word);
   uint32_t incl = pc;
 #pragma unroll
@@ -593,12 +676,7 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
     // Pass A: 32 consecutive symbols per thread -> one bitmap word; warp scan
     // of the ones.
     const uint32_t my0 = 32 * tid;
-    uint32_t word;
-    {
-      uint32_t u[8 * SB];
-      load_from_smem<SB, THREADS>(sIn, my0, u);
-      word = pack_bits<SB>(u, k) & valid_mask(my0, nv);
-    }
+    const uint32_t word = tile_word<SB, THREADS>(sIn, my0, k) & valid_mask(my0, nv);
     const uint32_t pc = __popc(word);
     uint32_t incl = pc;
 #pragma unroll
@@ -635,9 +713,16 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
     const uint32_t Zw = Zb + seg - Pw;        // zeros of level l before the warp
     const uint32_t Ow = R + Pw;               // ones of level l before the warp
     const bool one_node = pf == pl;
+    // nodes of the warp's first and last symbol (its segment is in node order)
+    uint32_t wpf = pf, wpl = pf;
+    if (!one_node && nvw) {
+      wpf = ((uint32_t)sInS[seg] & lmask) >> pshift;
+      wpl = ((uint32_t)sInS[seg + nvw - 1] & lmask) >> pshift;
+    }
+    const bool warp_one = one_node || wpf == wpl;  // the warp's symbols lie in one node
     uint32_t gz = 0, go = 0, zoff = 0, ooff = nzw * SB;  // destinations, staging offsets (bytes)
-    if (one_node) {
-      const uint2 tb = tab[pf];
+    if (warp_one && nvw) {
+      const uint2 tb = tab[wpf];
       gz = tb.x + Zw;
       go = tb.y + Ow;
       zoff = (gz * SB) & 15u;
@@ -697,13 +782,14 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
 
       // Phase 2: the warp writes its zeros and ones to T_{l+1}, counting the
       // next level's ones per destination tile.
+      const uint32_t mk1 = (SB == 1 ? 0x01010101u : SB == 2 ? 0x00010001u : 1u) << k1;
+      const uint64_t gend = (uint64_t)a.n * SB;
       if (one_node) {
-        // the whole tile lies in one node: its zeros and ones are two runs
+        // the whole tile lies in one node: its zeros and ones are two runs,
+        // counted per destination tile for the whole CTA
         const uint2 tb = tab[pf];
         const uint32_t r0 = tb.x + Zb, r1 = tb.y + R;  // where the tile's runs start
         const uint32_t s0 = ((r0 >> a.log2T) + 1) << a.log2T, s1 = ((r1 >> a.log2T) + 1) << a.log2T;
-        const uint32_t mk1 = (SB == 1 ? 0x01010101u : SB == 2 ? 0x00010001u : 1u) << k1;
-        const uint64_t gend = (uint64_t)a.n * SB;
         uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
         warp_copy_run<SB>(stage, zoff, a.out, (uint64_t)gz * SB, nzw * SB, gend, s0, mk1, k1, c0a, c0b);
         warp_copy_run<SB>(stage, ooff, a.out, (uint64_t)go * SB, tw * SB, gend, s1, mk1, k1, c1a, c1b);
@@ -721,28 +807,82 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
             sRun[1] = r1;
           }
         }
+      } else if (warp_one) {
+        // the warp's symbols lie in one node (the tile does not): two runs
+        // of at most 1024 symbols, each crossing at most one tile boundary
+        // of T_{l+1}; counted per warp
+        const uint32_t t0 = gz >> a.log2T, t1 = go >> a.log2T;
+        uint32_t c0a = 0, c0b = 0, c1a = 0, c1b = 0;
+        warp_copy_run<SB>(stage, zoff, a.out, (uint64_t)gz * SB, nzw * SB, gend, (t0 + 1) << a.log2T, mk1,
+                          k1, c0a, c0b);
+        warp_copy_run<SB>(stage, ooff, a.out, (uint64_t)go * SB, tw * SB, gend, (t1 + 1) << a.log2T, mk1,
+                          k1, c1a, c1b);
+        const uint32_t v0 = __reduce_add_sync(0xFFFFFFFFu, c0a);
+        const uint32_t v1 = __reduce_add_sync(0xFFFFFFFFu, c0b);
+        const uint32_t v2 = __reduce_add_sync(0xFFFFFFFFu, c1a);
+        const uint32_t v3 = __reduce_add_sync(0xFFFFFFFFu, c1b);
+        if (lane == 0) {
+          if (v0 && t0 < a.NT) counts_add(a.cout, t0, v0);
+          if (v1 && t0 + 1 < a.NT) counts_add(a.cout, t0 + 1, v1);
+          if (v2 && t1 < a.NT) counts_add(a.cout, t1, v2);
+          if (v3 && t1 + 1 < a.NT) counts_add(a.cout, t1 + 1, v3);
+        }
       } else {
+        // Several nodes in the warp: each symbol goes to the zero or one
+        // range of its own node.  Zeros (then ones) are staged in node order,
+        // so their destinations rise monotonically: ones are counted per run
+        // of equal destination tile, carried across groups, one flush per
+        // change of tile.  When the warp spans at most 32 nodes their table
+        // entries are fetched once, one per lane, and exchanged by shuffle.
         Sym *outS = reinterpret_cast<Sym *>(a.out);
+        const uint32_t span = wpl - wpf + 1;
+        const bool lanes_tab = wpl >= wpf && span <= 32;
+        uint2 mytab = make_uint2(0u, 0u);
+        if (lanes_tab && lane < span) mytab = tab[wpf + lane];
+        uint32_t cdt = 0xFFFFFFFFu, ccnt = 0;  // running destination tile and its ones
         for (uint32_t base = 0; base < nvw; base += 32) {
           const uint32_t kk = base + lane;
           const bool valid = kk < nvw;
-          uint32_t dest = 0xFFFFFFFFu, bit = 0;
-          if (valid) {
-            const Sym s = stageS[kk];
-            const uint32_t p = ((uint32_t)s & lmask) >> pshift;
-            const uint2 tb = tab[p];
-            dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
-            if (dest < a.n) outS[dest] = s;
-            else dest = 0xFFFFFFFFu;
-            bit = ((uint32_t)s >> k1) & 1u;
+          const Sym sv = valid ? stageS[kk] : (Sym)0;
+          const uint32_t p = ((uint32_t)sv & lmask) >> pshift;
+          uint2 tb;
+          if (lanes_tab) {
+            const uint32_t src = valid ? p - wpf : 0u;
+            tb.x = __shfl_sync(0xFFFFFFFFu, mytab.x, src);
+            tb.y = __shfl_sync(0xFFFFFFFFu, mytab.y, src);
+          } else {
+            tb = valid ? tab[p] : make_uint2(0u, 0u);
           }
-          const uint32_t dt = dest >> a.log2T;
-          const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit && dest != 0xFFFFFFFFu);
-          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dt);
-          const uint32_t c = __popc(ones & peers);
-          if (dest != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1) && c)
-            counts_add(a.cout, dt, c);
+          uint32_t dt = 0xFFFFFFFFu, bit = 0;
+          if (valid) {
+            const uint32_t dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
+            if (dest < a.n) {
+              outS[dest] = sv;
+              dt = dest >> a.log2T;
+              bit = ((uint32_t)sv >> k1) & 1u;
+            }
+          }
+          const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit);
+          const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, dt, 1);
+          uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || dt != prev);
+          while (heads) {  // warp-uniform: one step per run of equal dt
+            const uint32_t h = __ffs(heads) - 1;
+            heads &= heads - 1;
+            const uint32_t sdt = __shfl_sync(0xFFFFFFFFu, dt, h);
+            if (sdt == 0xFFFFFFFFu) continue;
+            const uint32_t nx = heads ? (uint32_t)__ffs(heads) - 1 : 32u;
+            const uint32_t seg_mask = (nx == 32 ? 0xFFFFFFFFu : (1u << nx) - 1u) & ~((1u << h) - 1u);
+            const uint32_t c = __popc(ones & seg_mask);
+            if (sdt == cdt) {
+              ccnt += c;
+            } else {
+              if (lane == 0 && ccnt) counts_add(a.cout, cdt, ccnt);
+              cdt = sdt;
+              ccnt = c;
+            }
+          }
         }
+        if (lane == 0 && ccnt) counts_add(a.cout, cdt, ccnt);
       }
     }
     if (ring_slot) *ring_slot = ring_value;
@@ -799,9 +939,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_sp
     // after all zeros of the level, which are n minus the level's ones,
     // summed from the top tier of the level's tile counts.
     if (tid < 32) {
-      uint32_t ones = 0;
-      for (uint32_t i = tid; i <= (a.NT - 1) >> 12; i += 32) ones += __ldcg(&a.cin.c2[i]);
-      ones = __reduce_add_sync(0xFFFFFFFFu, ones);
+      const uint32_t ones = counts_total_warp(a.cin, a.NT);
       if (tid == 0) sTab[0] = make_uint2(0u, a.n - ones);
     }
   } else if (tab_smem) {
