@@ -165,9 +165,11 @@ def measured_hbm_peak():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources the single-build kernels and their launches come
+    from (a committed ncu figure is used only while it matches)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1407_8142_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in ("wt_build.cu", "wt_dev.cuh", "wt_internal.h", "wt_kernels.cuh"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -406,6 +408,23 @@ def main_ours(args):
         per = s1.elapsed_time(e1) / (5 * R)
         latency = {"single_build_ms_median": float(np.median(singles)),
                    "graph_builds": R, "graph_build_ms": per, "graph_symbols_per_s": n / (per * 1e-3)}
+        # the same build as one persistent launch (the batched kernel with one tree)
+        if not matrix:
+            with wt.Batch([(n, sigma, sb)]) as bt:
+                bt.set_inputs([d_S])
+                bsingles = []
+                for _ in range(23):
+                    torch.cuda.synchronize(dev)
+                    s1.record(stream)
+                    bt.build(stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    bsingles.append(s1.elapsed_time(e1))
+                if bt.sync() != 0:
+                    raise SystemExit("single-launch build failed")
+                same = bool(np.array_equal(bt.tree(0).to_host()["bits"], tree.to_host()["bits"]))
+                latency.update({"one_launch_build_ms_median": float(np.median(bsingles[3:])),
+                                "one_launch_matches_plain": same})
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -668,6 +687,104 @@ def main_serve(args):
     return 0
 
 
+def main_query(args):
+    """Batched queries over one built tree (or matrix): m random access, rank
+    and select queries, one thread per query, timed with CUDA events."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1407_8142_gb300 import wt
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    C = CONFIGS[args.config]
+    sigma, sb = C["sigma"], C["b"]
+    n = args.n or C["n"]
+    S = config_input(args.config, n, args.seed)
+    matrix = args.shape == "matrix"
+    tree = (wt.WaveletMatrix if matrix else wt.WaveletTree)(n, sigma, sb)
+    tree.build(wt._torch_symbols(S))
+    if tree.sync() != 0:
+        raise SystemExit("build failed")
+    L = tree.info().levels
+    m = args.query_m
+    rng = np.random.default_rng(args.seed + 1)
+    idx_h = rng.integers(0, n, m).astype(np.uint64)
+    c_h = S[rng.integers(0, n, m)].astype(np.uint32)  # symbols that occur, as a text index would ask
+    idx = torch.from_numpy(idx_h.view(np.int64)).to(dev)
+    cs = torch.from_numpy(c_h.view(np.int32)).to(dev)
+    out32 = torch.empty(m, dtype=torch.int32, device=dev)
+    out64 = torch.empty(m, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # select asks for the occurrence of c at or before a random position
+    wt.wt_rank(tree.handle, cs.data_ptr(), idx.data_ptr(), m, out64.data_ptr(), stream)
+    ks = torch.clamp(out64.clone(), min=1)
+    calls = {
+        "access": lambda: wt.wt_access(tree.handle, idx.data_ptr(), m, out32.data_ptr(), stream),
+        "rank": lambda: wt.wt_rank(tree.handle, cs.data_ptr(), idx.data_ptr(), m, out64.data_ptr(), stream),
+        "select": lambda: wt.wt_select(tree.handle, cs.data_ptr(), ks.data_ptr(), m, out64.data_ptr(), stream),
+    }
+    res = {}
+    with ClockSampler(0) as clocks:
+        for name, fn in calls.items():
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = s0.elapsed_time(s1) / args.steps
+            res[name] = {"queries_per_s": m / (ms * 1e-3), "ms_per_batch": ms}
+    if tree.sync() != 0:
+        raise SystemExit("queries failed")
+    # Sector model (32-byte sectors a query must touch, tables and samples of
+    # the top levels being cache-resident): one rank = 2 sectors (directory
+    # entry, bitmap word); one select = 6 (two samples, ~3 binary-search
+    # steps, the word).  Tree: access L ranks, rank L+1 ranks and a node
+    # start, select L selects, a rank and node starts.  Matrix: access L
+    # ranks, rank 2L ranks, select 2L ranks and L selects.
+    peak, peak_kind = measured_hbm_peak()
+    if matrix:
+        sect = {"access": 2 * L, "rank": 4 * L, "select": 4 * L + 6 * L}
+    else:
+        sect = {"access": 2 * L, "rank": 2 * (L + 1) + 1, "select": 6 * L + 2 + 2}
+    sect = {k: 32 * v for k, v in sect.items()}
+    for name in res:
+        res[name]["sector_bytes_per_query"] = sect[name]
+        res[name]["sector_gbs"] = round(res[name]["queries_per_s"] * sect[name] / 1e9, 1)
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import serialwt
+        serialwt.build_oracle()
+        kq = 16
+        t0 = time.perf_counter()
+        serialwt.rank(S, sigma, c_h[:kq], idx_h[:kq])
+        dt = time.perf_counter() - t0
+        cpu = {"value": kq / dt, "unit": "rank queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{kq} rank queries on the same tree's input (naive scans over S, 1 thread)"}
+    line = {"metric": ("wavelet matrix" if matrix else "wavelet tree") + " rank queries/s (batched, one per thread)",
+            "value": res["rank"]["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["rank"]["ms_per_batch"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": workload_config({"structure": "wavelet matrix (Section 7)" if matrix
+                                       else "levelwise wavelet tree (Fig. 1)",
+                                       "queries_per_batch": m, "query_mix": "uniform positions, "
+                                       "symbols drawn from the sequence"}, cfg=args.config, n=n),
+            "roofline": {"bound": "hbm", "achieved": res["rank"]["sector_gbs"], "peak": peak,
+                         "unit": "GB/s", "frac": round(res["rank"]["sector_gbs"] / peak, 4), "traffic": None,
+                         "kernel": "k_rank (random 32-byte sectors, counted per query)",
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy-based)"},
+            "queries": res, "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps,
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    tree.free()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -685,9 +802,10 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["levelwt", "batch", "serve"], default="levelwt",
+    ap.add_argument("--workload", choices=["levelwt", "batch", "serve", "query"], default="levelwt",
                     help="levelwt: one build of n symbols (default); batch: the 4096-sequence batched "
-                         "build; serve: the request-serving trace")
+                         "build; serve: the request-serving trace; query: batched access/rank/select")
+    ap.add_argument("--query-m", type=int, default=1 << 24, help="queries per batch (query workload)")
     ap.add_argument("--batch-m", type=int, default=4096)
     ap.add_argument("--serve-horizon", type=float, default=10.0)
     ap.add_argument("--serve-inflight", type=int, default=4)
@@ -702,6 +820,8 @@ def main(argv=None):
         return main_batch(args)
     if args.workload == "serve":
         return main_serve(args)
+    if args.workload == "query":
+        return main_query(args)
     return main_ours(args)
 
 

@@ -120,6 +120,7 @@ int wt_batch_create(const wt_seq_desc *descs, uint32_t m, const wt_config *cfg, 
     v->d_rank = t.rank;
     v->d_zeros = t.zeros;
     v->d_node_start = t.node_start;
+    v->d_tab = t.tab;
     v->d_ctrl = reinterpret_cast<uint32_t *>(t.err) - kCtrlErr;  // d_ctrl + kCtrlErr is the tree's error word
     b->views[i] = v;
   }
@@ -154,6 +155,7 @@ int wt_batch_build(wt_batch *b, void *stream) {
   for (wt_tree *v : b->views) {
     v->stream = st;
     v->sticky_error = 0;
+    ++v->build_count;  // invalidates a query index built for the previous contents
   }
   WT_CUDA(cudaMemsetAsync(b->d_ctrl, 0, b->ctrl_bytes, st));
   BatchArgs a;

@@ -51,8 +51,18 @@ struct wt_tree {
   int sticky_error = 0;
   void *owner = nullptr;          // set for views of trees owned by a batch or a server
 
+  // query index: sampled select positions per level (built on first select
+  // after a build, owned by the tree object itself, also for views)
+  uint32_t *d_sel = nullptr;
+  uint64_t sel_stride = 0;        // entries per (level, bit value)
+  uint32_t sel_for = 0;           // build_count + 1 the index was built for (0 = none)
+
   bool profile = false;
   cudaEvent_t *ev = nullptr;      // 2 * kMaxProfiled events, created on first use
   int32_t *ev_kind = nullptr;
   int n_ev = 0;                   // launches recorded since wt_profile(tree, 1)
+
+  ~wt_tree() {
+    if (d_sel) cudaFree(d_sel);
+  }
 };

@@ -170,6 +170,7 @@ int launch_slot(wt_server *srv, Slot &s) {
     v->d_rank = t.rank;
     v->d_zeros = t.zeros;
     v->d_node_start = t.node_start;
+    v->d_tab = t.tab;
     v->d_ctrl = reinterpret_cast<uint32_t *>(t.err) - kCtrlErr;
     v->stream = s.st;
     v->sticky_error = 0;

@@ -81,6 +81,16 @@ def test_batch_views_answer_queries_and_are_owned(wt):
         c = S[::7].astype(np.uint32)
         r = v.rank(c, idx).cpu().numpy().view(np.uint64)
         assert np.array_equal(r, serialwt.rank(S, 65536, c, idx))
+        assert np.array_equal(v.select(c, r).cpu().numpy().view(np.uint64), idx)
+        # a rebuild from other inputs invalidates the view's select index
+        S2 = synth.uniform(S.size, 65536, 2, 8)
+        b.set_inputs([S2, T])
+        b.build()
+        assert b.sync() == 0
+        c2 = S2[::7].astype(np.uint32)
+        r2 = v.rank(c2, idx).cpu().numpy().view(np.uint64)
+        assert np.array_equal(r2, serialwt.rank(S2, 65536, c2, idx))
+        assert np.array_equal(v.select(c2, r2).cpu().numpy().view(np.uint64), idx)
         # a view belongs to its batch
         assert wt.load().wt_free(v.handle) == wt.WT_ERR_ARG
 

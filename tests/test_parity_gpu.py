@@ -188,6 +188,33 @@ def test_queries(wt, sigma, b, n):
         assert np.array_equal(s_gpu, s_ref)
 
 
+@pytest.mark.parametrize("shape", ["tree", "matrix"])
+@pytest.mark.parametrize("sigma,b", [(256, 1), (1 << 20, 4)])
+def test_queries_at_scale(wt, shape, sigma, b):
+    """n = 2^24 + 123 (several thousand directory blocks, sampled select
+    index with many samples): sampled queries against the oracle, and a
+    rebuild from another input invalidates the select index."""
+    n = (1 << 24) + 123
+    cls = wt.WaveletMatrix if shape == "matrix" else wt.WaveletTree
+    with cls(n, sigma, b) as t:
+        for seed in (21, 22):
+            S = synth.zipf(n, sigma, 1.0, b, seed)
+            t.build(S)
+            assert t.sync() == 0
+            rng = np.random.default_rng(seed)
+            idx = np.concatenate([rng.integers(0, n, 300), [0, n - 1]]).astype(np.uint64)
+            assert np.array_equal(t.access(idx).cpu().numpy().view(np.uint32),
+                                  S[idx.astype(np.int64)].astype(np.uint32))
+            c = np.concatenate([S[rng.integers(0, n, 150)].astype(np.uint32),
+                                rng.integers(0, sigma, 50).astype(np.uint32)])
+            ii = rng.integers(0, n, c.size).astype(np.uint64)
+            r_ref = serialwt.rank(S, sigma, c, ii)
+            assert np.array_equal(t.rank(c, ii).cpu().numpy().view(np.uint64), r_ref)
+            k = np.maximum(r_ref, 1).astype(np.uint64)
+            s_ref = serialwt.select(S, sigma, c, k)
+            assert np.array_equal(t.select(c, k).cpu().numpy().view(np.uint64), s_ref)
+
+
 def test_config1_full(wt):
     """n = 2^20 uint8, uniform over 256 symbols, seed 0: the whole output."""
     S, sigma = synth.config1(0)
