@@ -827,32 +827,79 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
           if (v2 && t1 < a.NT) counts_add(a.cout, t1, v2);
           if (v3 && t1 + 1 < a.NT) counts_add(a.cout, t1 + 1, v3);
         }
-      } else {
-        // Several nodes in the warp: each symbol goes to the zero or one
-        // range of its own node.  Zeros (then ones) are staged in node order,
-        // so their destinations rise monotonically: ones are counted per run
-        // of equal destination tile, carried across groups, one flush per
-        // change of tile.  When the warp spans at most 32 nodes their table
-        // entries are fetched once, one per lane, and exchanged by shuffle.
+      } else if (wpl >= wpf && wpl - wpf < 32) {
+        // Several nodes in the warp, at most 32: the staging holds, for each
+        // node in order, its zeros, then (after all zeros) its ones; each
+        // is one run with one destination.  Lane q finds where node wpf+q
+        // starts in the warp's input (binary search over the input, which
+        // is in node order) and, from the bit words, how many zeros and
+        // ones precede it; then the warp copies the runs node by node.
         Sym *outS = reinterpret_cast<Sym *>(a.out);
         const uint32_t span = wpl - wpf + 1;
-        const bool lanes_tab = wpl >= wpf && span <= 32;
-        uint2 mytab = make_uint2(0u, 0u);
-        if (lanes_tab && lane < span) mytab = tab[wpf + lane];
+        auto zeros_before = [&](uint32_t x) -> uint32_t {  // zeros of the warp before input position x
+          if (x >= nvw) return nzw;
+          const uint2 wv = sWP[32 * warp + (x >> 5)];
+          return x - (wv.y + __popc(wv.x & ((1u << (x & 31)) - 1u)));
+        };
+        uint32_t f = nvw;  // first input position of node wpf + lane
+        if (lane < span) {
+          uint32_t lo = 0, hi = nvw;
+          if (lane == 0) hi = 0;
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((((uint32_t)sInS[seg + mid] & lmask) >> pshift) < wpf + lane) lo = mid + 1;
+            else hi = mid;
+          }
+          f = lo;
+        }
+        const uint32_t fnext = __shfl_down_sync(0xFFFFFFFFu, f, 1);
+        const uint32_t fe = lane + 1 < span ? fnext : nvw;
+        const uint32_t zs = zeros_before(f), ze = zeros_before(fe);
+        const uint2 tb = lane < span ? tab[wpf + lane] : make_uint2(0u, 0u);
+        const uint32_t gzq = tb.x + Zw + zs;         // destination of the node's zeros
+        const uint32_t goq = tb.y + Ow + (f - zs);   // destination of the node's ones
+        const uint32_t zrun = ze - zs, orun = (fe - ze) - (f - zs);
+        for (uint32_t q = 0; q < span; ++q) {
+#pragma unroll
+          for (uint32_t part = 0; part < 2; ++part) {
+            const uint32_t len = __shfl_sync(0xFFFFFFFFu, part ? orun : zrun, q);
+            if (len == 0) continue;
+            const uint32_t src = __shfl_sync(0xFFFFFFFFu, part ? nzw + (f - zs) : zs, q);
+            const uint32_t dst = __shfl_sync(0xFFFFFFFFu, part ? goq : gzq, q);
+            const uint32_t dt = dst >> a.log2T, bnd = (dt + 1) << a.log2T;
+            uint32_t ca = 0, cb = 0;
+            for (uint32_t e = lane; e < len; e += 32) {
+              const Sym v = stageS[src + e];
+              const uint32_t d = dst + e;
+              if (d < a.n) {
+                outS[d] = v;
+                const uint32_t one = ((uint32_t)v >> k1) & 1u;
+                if (d < bnd) ca += one;
+                else cb += one;
+              }
+            }
+            ca = __reduce_add_sync(0xFFFFFFFFu, ca);
+            cb = __reduce_add_sync(0xFFFFFFFFu, cb);
+            if (lane == 0) {
+              if (ca && dt < a.NT) counts_add(a.cout, dt, ca);
+              if (cb && dt + 1 < a.NT) counts_add(a.cout, dt + 1, cb);
+            }
+          }
+        }
+      } else {
+        // More than 32 nodes in the warp: each symbol goes to the zero or
+        // one range of its own node.  Zeros (then ones) are staged in node
+        // order, so their destinations rise monotonically: ones are counted
+        // per run of equal destination tile, carried across groups, one
+        // flush per change of tile.
+        Sym *outS = reinterpret_cast<Sym *>(a.out);
         uint32_t cdt = 0xFFFFFFFFu, ccnt = 0;  // running destination tile and its ones
         for (uint32_t base = 0; base < nvw; base += 32) {
           const uint32_t kk = base + lane;
           const bool valid = kk < nvw;
           const Sym sv = valid ? stageS[kk] : (Sym)0;
           const uint32_t p = ((uint32_t)sv & lmask) >> pshift;
-          uint2 tb;
-          if (lanes_tab) {
-            const uint32_t src = valid ? p - wpf : 0u;
-            tb.x = __shfl_sync(0xFFFFFFFFu, mytab.x, src);
-            tb.y = __shfl_sync(0xFFFFFFFFu, mytab.y, src);
-          } else {
-            tb = valid ? tab[p] : make_uint2(0u, 0u);
-          }
+          const uint2 tb = valid ? tab[p] : make_uint2(0u, 0u);
           uint32_t dt = 0xFFFFFFFFu, bit = 0;
           if (valid) {
             const uint32_t dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
