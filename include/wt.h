@@ -125,7 +125,10 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
  * Fig. 1): a pre-pass that histograms the symbols, checks their range and
  * counts level 0's ones per tile, the node tables, one split pass per level
  * l = 0..L-2 (bits, directory and the stable split into T_{l+1}), and a last
- * pass for level L-1 (bits and directory).  Every size is known on the host, so the call has no host
+ * pass for level L-1 (bits and directory).  For sigma > 2^13 the pre-pass
+ * builds no histogram: each split pass counts, per child node, the ones of
+ * the next level, and a small kernel before each level turns these counts
+ * into that level's node tables and node starts.  Every size is known on the host, so the call has no host
  * synchronisation and may be captured into a CUDA graph.
  * d_seq is read-only; it must stay valid until the stream work completes.
  * A d_seq that is not 16-byte aligned is first copied into tree scratch.
@@ -207,7 +210,8 @@ int wt_select(const wt_tree *tree, const uint32_t *d_c, const uint64_t *d_k, uin
  * to 2048 launches per window).  wt_profile_read, after wt_sync, returns the
  * number of launches recorded in the window and fills up to `cap` entries of
  * ms[] with each launch's duration and kind[] with its kind: 0 pre-pass,
- * 1 histogram scan, 2 node tables, 3 split pass, 4 last-level pass.
+ * 1 node starts (histogram scan, or the last two levels' starts from node
+ * counts), 2 node tables, 3 split pass, 4 last-level pass.
  * wt_profile(tree, 0) stops recording.
  */
 int wt_profile(wt_tree *tree, int enable);

@@ -129,7 +129,9 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     a.W = tr.W;
     a.tab = tr.tab + ((1u << level) - 1);
     a.pshift = L - level;
-    a.matrix = 0;
+    a.count_table = 0;
+    a.tab_out = nullptr;
+    a.nones_next = nullptr;
     a.lo = lo;
     a.cin = tree_counts(tr, level);
     a.cout = tree_counts(tr, level + 1);

@@ -159,7 +159,7 @@ int launch_prepass(Launcher &ln, const uint8_t *in, bool in_padded) {
   const uint32_t nbins = 1u << t->L;
   ln.before(kPrepass);
   int rc;
-  if (t->shape == WT_SHAPE_MATRIX)
+  if (t->shape == WT_SHAPE_MATRIX || t->node_counts)
     rc = launch_persistent(ln, k_prepass<SB, THREADS, kHistNone>, THREADS, prepass_smem_bytes<SB, THREADS>(0), a);
   else if (nbins <= kHistLanesMaxBins)
     rc = launch_persistent(ln, k_prepass<SB, THREADS, kHistLanes>, THREADS,
@@ -220,9 +220,14 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.log2T = 5 + (uint32_t)__builtin_ctz(THREADS);
   a.W = t->W;
   const bool matrix = t->shape == WT_SHAPE_MATRIX;
-  a.tab = matrix ? nullptr : t->d_tab + ((1u << level) - 1);
+  // one node whose table comes from the tile counts: the matrix, and level 0
+  // of a tree whose tables come from node counts
+  const bool count_table = matrix || (t->node_counts && level == 0);
+  a.tab = count_table ? nullptr : t->d_tab + ((1u << level) - 1);
   a.pshift = matrix ? t->L : t->L - level;
-  a.matrix = matrix ? 1 : 0;
+  a.count_table = count_table ? 1 : 0;
+  a.tab_out = (t->node_counts && level == 0) ? t->d_tab : nullptr;
+  a.nones_next = t->node_counts ? t->d_hist + ((2u << level) - 1) : nullptr;
   a.lo = ln.out(level);
   a.cin = ln.counts(level);
   a.cout = ln.counts(level + 1);
@@ -275,21 +280,62 @@ int launch_tables(Launcher &ln) {
   return WT_OK;
 }
 
+// Tables of level m (1 <= m <= L-2) from the node counts of the previous
+// split pass; m = L-1: node starts of the last two levels only.
+int launch_node_tables(Launcher &ln, uint32_t m) {
+  wt_tree *t = ln.t;
+  const uint32_t L = t->L;
+  const uint2 *tab_prev = t->d_tab + ((1u << (m - 1)) - 1);
+  const uint32_t *ones = t->d_hist + ((1u << m) - 1);
+  if (m + 1 < L) {
+    NodeTabArgs a;
+    a.ones = ones;
+    a.tab_prev = tab_prev;
+    a.tab = t->d_tab + ((1u << m) - 1);
+    a.E = t->d_node_start;
+    a.L = L;
+    a.m = m;
+    a.n = (uint32_t)t->n;
+    a.nblocks = ((1u << m) + kScanChunk - 1) / kScanChunk;
+    a.ticket = ln.ticket();
+    a.lb = ln.lb();
+    ln.before(kTables);
+    k_node_tables<<<a.nblocks, kScanThreads, 0, ln.st>>>(a);
+  } else {
+    LeafStartArgs a;
+    a.ones = ones;
+    a.tab_prev = tab_prev;
+    a.E = t->d_node_start;
+    a.L = L;
+    a.n = (uint32_t)t->n;
+    const uint32_t cnt = 1u << (L - 1);
+    ln.before(kHistScan);
+    k_leaf_starts<<<std::min<uint32_t>((cnt + 255) / 256, 4096u), 256, 0, ln.st>>>(a);
+  }
+  ln.after();
+  ++ln.pass;
+  WT_CUDA(cudaGetLastError());
+  return WT_OK;
+}
+
 template <int SB, int THREADS>
 int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
   Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
   int rc;
   if ((rc = launch_prepass<SB, THREADS>(ln, seq, seq_padded))) return rc;
-  if (t->shape == WT_SHAPE_TREE && (rc = launch_tables(ln))) return rc;
+  if (t->shape == WT_SHAPE_TREE && !t->node_counts && (rc = launch_tables(ln))) return rc;
   if (t->L == 0) return WT_OK;
   const uint8_t *in = seq;
   bool padded = seq_padded;
   for (uint32_t l = 0; l + 1 < t->L; ++l) {
+    // with node counts, the tables of level l come from the pass over l-1
+    if (t->node_counts && l >= 1 && (rc = launch_node_tables(ln, l))) return rc;
     uint8_t *out = static_cast<uint8_t *>(t->d_buf[l & 1]);
     if ((rc = launch_split<SB, THREADS>(ln, in, padded, out, l))) return rc;
     in = out;
     padded = true;
   }
+  if (t->node_counts && (rc = launch_node_tables(ln, t->L - 1))) return rc;
   return launch_leaf<SB, THREADS>(ln, in, padded, t->L - 1);
 }
 
@@ -369,6 +415,9 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   t->sb = symbol_bytes;
   t->L = L;
   t->shape = shape;
+  // large alphabets: per-node counts kept by the split passes replace the
+  // 2^L-bin histogram (whose global atomics serialise on hot symbols)
+  t->node_counts = shape == WT_SHAPE_TREE && (1ull << L) > kHistSmemMaxBins;
   t->NB = (n + 511) / 512;
   t->W = 16 * t->NB;
   t->threads = pick_threads(n, symbol_bytes, t->sms, t->cfg.tile_threads);
@@ -564,7 +613,8 @@ int wt_kernels_per_build(const wt_tree *t) {
   if (!t) return WT_ERR_ARG;
   if (t->n == 0) return 0;
   int k = 1;                                              // pre-pass
-  if (t->shape == WT_SHAPE_TREE) k += 1 + (tables_blocks(t->L) ? 1 : 0);  // histogram scan, tables
+  if (t->node_counts) k += (int)t->L - 1;                 // node tables, levels 1..L-1
+  else if (t->shape == WT_SHAPE_TREE) k += 1 + (tables_blocks(t->L) ? 1 : 0);  // histogram scan, tables
   if (t->L >= 1) k += (int)(t->L - 1) + 1;    // splits + last level
   return k;
 }

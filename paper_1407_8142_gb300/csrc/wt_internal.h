@@ -8,9 +8,9 @@
 namespace wtk {
 
 constexpr uint32_t kMaxLevels = 26;     // 2^L histogram bins must fit comfortably
-constexpr uint32_t kPasses = 32;        // ticket counters per build (passes <= 3 + L)
-constexpr uint32_t kCtrlWords = 64;     // [0,32) tickets, [32] error, rest reserved
-constexpr uint32_t kCtrlErr = 32;
+constexpr uint32_t kPasses = 64;        // ticket counters per build (passes <= 2L + 3)
+constexpr uint32_t kCtrlWords = 128;    // [0,64) tickets, [64] error, rest reserved
+constexpr uint32_t kCtrlErr = 64;
 constexpr uint32_t kMaxProfiled = 2048;  // kernel launches recorded per profiling window
 
 enum KernelKind : int32_t { kPrepass = 0, kHistScan = 1, kTables = 2, kSplit = 3, kLeaf = 4 };
@@ -21,6 +21,9 @@ struct wt_tree {
   uint64_t n = 0;
   uint32_t sigma = 0, sb = 0, L = 0;
   uint32_t shape = WT_SHAPE_TREE;  // WT_SHAPE_TREE or WT_SHAPE_MATRIX
+  // tree with a large alphabet: node sizes come from per-node counts kept by
+  // the split passes instead of a 2^L-bin histogram of the input
+  bool node_counts = false;
   uint64_t W = 0, NB = 0;
   uint32_t threads = 0;         // CTA size of the level passes
   uint64_t T = 0;               // symbols per tile
@@ -35,7 +38,8 @@ struct wt_tree {
   unsigned long long *d_node_start = nullptr;
   // scratch
   uint2 *d_tab = nullptr;       // per level l (heap offset 2^l - 1): {O_l[p], E_{l+1}[2p+1]-O_l[p]}
-  uint32_t *d_ctrl = nullptr;   // kCtrlWords control words followed by the 2^L histogram (tree)
+  uint32_t *d_ctrl = nullptr;   // kCtrlWords control words, then 2^L words: the histogram
+                                // (tree) or the per-node ones counters (node_counts)
   uint32_t *d_hist = nullptr;
   uint32_t *d_counts = nullptr;   // per level: ones per tile, per 64 tiles, per 4096 tiles
   uint64_t counts_per_level = 0;

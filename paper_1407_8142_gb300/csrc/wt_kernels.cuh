@@ -527,7 +527,10 @@ struct SplitArgs {
   uint64_t W;
   const uint2 *tab;    // this level's {O_l[p], E_{l+1}[2p+1] - O_l[p]}
   uint32_t pshift;     // node prefix = symbol >> pshift (L - level; L for the matrix)
-  int matrix;          // wavelet matrix: one node, table {0, zeros of level l}
+  int count_table;     // one node whose table {0, zeros of the level} comes from the
+                       // level's tile counts (wavelet matrix; tree level 0 with node counts)
+  uint2 *tab_out;      // if set, CTA 0 also stores that one-node table there
+  uint32_t *nones_next;  // if set, ones of level l+1 per child node (2p + bit) are added here
   LevelOut lo;
   TileCounts cin;      // ones of level l per tile of T_l
   TileCounts cout;     // ones of level l+1 per tile of T_{l+1} (accumulated here)
@@ -637,6 +640,196 @@ constexpr uint32_t split_smem_bytes() {
          8u * (THREADS / 32) + 8u * kTabSmem + 192u;
 }
 
+// Phase C of a warp whose symbols span several nodes (the tile is not in
+// one node either): each symbol goes to the zero or one range of its own
+// node.  wWP is the warp's {bit word, ones before the word} array.
+//   1-byte symbols: symbol by symbol (small alphabets have few multi-node
+//     warps, and this form keeps the single-node path's registers intact;
+//     node counts never apply, sigma <= 256).
+//   wider symbols, at most 32 nodes in the warp: one run per node and part.
+//   more nodes: symbol by symbol.
+template <int SB>
+__device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint32_t log2T, uint32_t NT,
+                                              TileCounts cout, uint32_t *nones_next, const uint2 *tab,
+                                              const typename SymT<SB>::type *sInS,
+                                              const typename SymT<SB>::type *stageS, const uint2 *wWP,
+                                              uint32_t seg, uint32_t nvw, uint32_t nzw, uint32_t wpf,
+                                              uint32_t wpl, uint32_t Zw, uint32_t Ow, uint32_t lmask,
+                                              uint32_t pshift, uint32_t k1) {
+  using Sym = typename SymT<SB>::type;
+  const uint32_t lane = threadIdx.x & 31;
+  if constexpr (SB == 1) {
+    // Zeros (then ones) are staged in node order, so their destinations
+    // rise monotonically: ones are counted per run of equal destination
+    // tile, carried across groups, one flush per change of tile.  When the
+    // warp spans at most 32 nodes their table entries are fetched once, one
+    // per lane, and exchanged by shuffle.
+    (void)sInS;
+    (void)wWP;
+    (void)nones_next;
+    Sym *outS = reinterpret_cast<Sym *>(out);
+    const uint32_t span = wpl - wpf + 1;
+    const bool lanes_tab = wpl >= wpf && span <= 32;
+    uint2 mytab = make_uint2(0u, 0u);
+    if (lanes_tab && lane < span) mytab = tab[wpf + lane];
+    uint32_t cdt = 0xFFFFFFFFu, ccnt = 0;  // running destination tile and its ones
+    for (uint32_t base = 0; base < nvw; base += 32) {
+      const uint32_t kk = base + lane;
+      const bool valid = kk < nvw;
+      const Sym sv = valid ? stageS[kk] : (Sym)0;
+      const uint32_t p = ((uint32_t)sv & lmask) >> pshift;
+      uint2 tb;
+      if (lanes_tab) {
+        const uint32_t src = valid ? p - wpf : 0u;
+        tb.x = __shfl_sync(0xFFFFFFFFu, mytab.x, src);
+        tb.y = __shfl_sync(0xFFFFFFFFu, mytab.y, src);
+      } else {
+        tb = valid ? tab[p] : make_uint2(0u, 0u);
+      }
+      uint32_t dt = 0xFFFFFFFFu, bit = 0;
+      if (valid) {
+        const uint32_t dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
+        if (dest < n) {
+          outS[dest] = sv;
+          dt = dest >> log2T;
+          bit = ((uint32_t)sv >> k1) & 1u;
+        }
+      }
+      const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit);
+      const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, dt, 1);
+      uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || dt != prev);
+      while (heads) {  // warp-uniform: one step per run of equal dt
+        const uint32_t h = __ffs(heads) - 1;
+        heads &= heads - 1;
+        const uint32_t sdt = __shfl_sync(0xFFFFFFFFu, dt, h);
+        if (sdt == 0xFFFFFFFFu) continue;
+        const uint32_t nx = heads ? (uint32_t)__ffs(heads) - 1 : 32u;
+        const uint32_t seg_mask = (nx == 32 ? 0xFFFFFFFFu : (1u << nx) - 1u) & ~((1u << h) - 1u);
+        const uint32_t c = __popc(ones & seg_mask);
+        if (sdt == cdt) {
+          ccnt += c;
+        } else {
+          if (lane == 0 && ccnt) counts_add(cout, cdt, ccnt);
+          cdt = sdt;
+          ccnt = c;
+        }
+      }
+    }
+    if (lane == 0 && ccnt) counts_add(cout, cdt, ccnt);
+  } else if (wpl >= wpf && wpl - wpf < 32) {
+    // Several nodes in the warp, at most 32: the staging holds, for each
+    // node in order, its zeros, then (after all zeros) its ones; each
+    // is one run with one destination.  Lane q finds where node wpf+q
+    // starts in the warp's input (binary search over the input, which
+    // is in node order) and, from the bit words, how many zeros and
+    // ones precede it; then the warp copies the runs node by node.
+    Sym *outS = reinterpret_cast<Sym *>(out);
+    const uint32_t span = wpl - wpf + 1;
+    auto zeros_before = [&](uint32_t x) -> uint32_t {  // zeros of the warp before input position x
+      if (x >= nvw) return nzw;
+      const uint2 wv = wWP[x >> 5];
+      return x - (wv.y + __popc(wv.x & ((1u << (x & 31)) - 1u)));
+    };
+    uint32_t f = nvw;  // first input position of node wpf + lane
+    if (lane < span) {
+      uint32_t lo = 0, hi = nvw;
+      if (lane == 0) hi = 0;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((((uint32_t)sInS[seg + mid] & lmask) >> pshift) < wpf + lane) lo = mid + 1;
+        else hi = mid;
+      }
+      f = lo;
+    }
+    const uint32_t fnext = __shfl_down_sync(0xFFFFFFFFu, f, 1);
+    const uint32_t fe = lane + 1 < span ? fnext : nvw;
+    const uint32_t zs = zeros_before(f), ze = zeros_before(fe);
+    const uint2 tb = lane < span ? tab[wpf + lane] : make_uint2(0u, 0u);
+    const uint32_t gzq = tb.x + Zw + zs;         // destination of the node's zeros
+    const uint32_t goq = tb.y + Ow + (f - zs);   // destination of the node's ones
+    const uint32_t zrun = ze - zs, orun = (fe - ze) - (f - zs);
+    for (uint32_t q = 0; q < span; ++q) {
+#pragma unroll
+      for (uint32_t part = 0; part < 2; ++part) {
+        const uint32_t len = __shfl_sync(0xFFFFFFFFu, part ? orun : zrun, q);
+        if (len == 0) continue;
+        const uint32_t src = __shfl_sync(0xFFFFFFFFu, part ? nzw + (f - zs) : zs, q);
+        const uint32_t dst = __shfl_sync(0xFFFFFFFFu, part ? goq : gzq, q);
+        const uint32_t dt = dst >> log2T, bnd = (dt + 1) << log2T;
+        uint32_t ca = 0, cb = 0;
+        for (uint32_t e = lane; e < len; e += 32) {
+          const Sym v = stageS[src + e];
+          const uint32_t d = dst + e;
+          if (d < n) {
+            outS[d] = v;
+            const uint32_t one = ((uint32_t)v >> k1) & 1u;
+            if (d < bnd) ca += one;
+            else cb += one;
+          }
+        }
+        ca = __reduce_add_sync(0xFFFFFFFFu, ca);
+        cb = __reduce_add_sync(0xFFFFFFFFu, cb);
+        if (lane == 0) {
+          if (ca && dt < NT) counts_add(cout, dt, ca);
+          if (cb && dt + 1 < NT) counts_add(cout, dt + 1, cb);
+          if (nones_next && ca + cb) atomicAdd(&nones_next[2 * (wpf + q) + part], ca + cb);
+        }
+      }
+    }
+  } else {
+    // More than 32 nodes in the warp: each symbol goes to the zero or
+    // one range of its own node.  Zeros (then ones) are staged in node
+    // order, so their destinations rise monotonically: ones are counted
+    // per run of equal destination tile, carried across groups, one
+    // flush per change of tile.
+    Sym *outS = reinterpret_cast<Sym *>(out);
+    uint32_t cdt = 0xFFFFFFFFu, ccnt = 0;  // running destination tile and its ones
+    for (uint32_t base = 0; base < nvw; base += 32) {
+      const uint32_t kk = base + lane;
+      const bool valid = kk < nvw;
+      const Sym sv = valid ? stageS[kk] : (Sym)0;
+      const uint32_t p = ((uint32_t)sv & lmask) >> pshift;
+      const uint2 tb = valid ? tab[p] : make_uint2(0u, 0u);
+      uint32_t dt = 0xFFFFFFFFu, bit = 0;
+      if (valid) {
+        const uint32_t dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
+        if (dest < n) {
+          outS[dest] = sv;
+          dt = dest >> log2T;
+          bit = ((uint32_t)sv >> k1) & 1u;
+        }
+      }
+      const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit);
+      if (nones_next) {  // ones of level l+1 per child node 2p + bit
+        const uint32_t child = dt != 0xFFFFFFFFu ? 2 * p + (kk >= nzw ? 1u : 0u) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, child);
+        const uint32_t c = __popc(ones & peers);
+        if (child != 0xFFFFFFFFu && c && lane == (uint32_t)(__ffs(peers) - 1))
+          atomicAdd(&nones_next[child], c);
+      }
+      const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, dt, 1);
+      uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || dt != prev);
+      while (heads) {  // warp-uniform: one step per run of equal dt
+        const uint32_t h = __ffs(heads) - 1;
+        heads &= heads - 1;
+        const uint32_t sdt = __shfl_sync(0xFFFFFFFFu, dt, h);
+        if (sdt == 0xFFFFFFFFu) continue;
+        const uint32_t nx = heads ? (uint32_t)__ffs(heads) - 1 : 32u;
+        const uint32_t seg_mask = (nx == 32 ? 0xFFFFFFFFu : (1u << nx) - 1u) & ~((1u << h) - 1u);
+        const uint32_t c = __popc(ones & seg_mask);
+        if (sdt == cdt) {
+          ccnt += c;
+        } else {
+          if (lane == 0 && ccnt) counts_add(cout, cdt, ccnt);
+          cdt = sdt;
+          ccnt = c;
+        }
+      }
+    }
+    if (lane == 0 && ccnt) counts_add(cout, cdt, ccnt);
+  }
+}
+
 // Shared-memory working set of one split tile.
 struct SplitShared {
   uint8_t *stage;  // per-warp staging areas
@@ -644,6 +837,7 @@ struct SplitShared {
   uint2 *wt;       // per warp {ones, prefix share}
   uint32_t *cnt;   // 4 run counters
   uint32_t *run;   // 2 run starts
+  uint32_t *nc;    // node-count cache of thread 0: {node, ones of child 2 node, of child 2 node + 1}
 };
 
 // One tile of the split pass over level a.level: bits and directory of the
@@ -826,110 +1020,14 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
           if (v1 && t0 + 1 < a.NT) counts_add(a.cout, t0 + 1, v1);
           if (v2 && t1 < a.NT) counts_add(a.cout, t1, v2);
           if (v3 && t1 + 1 < a.NT) counts_add(a.cout, t1 + 1, v3);
-        }
-      } else if (wpl >= wpf && wpl - wpf < 32) {
-        // Several nodes in the warp, at most 32: the staging holds, for each
-        // node in order, its zeros, then (after all zeros) its ones; each
-        // is one run with one destination.  Lane q finds where node wpf+q
-        // starts in the warp's input (binary search over the input, which
-        // is in node order) and, from the bit words, how many zeros and
-        // ones precede it; then the warp copies the runs node by node.
-        Sym *outS = reinterpret_cast<Sym *>(a.out);
-        const uint32_t span = wpl - wpf + 1;
-        auto zeros_before = [&](uint32_t x) -> uint32_t {  // zeros of the warp before input position x
-          if (x >= nvw) return nzw;
-          const uint2 wv = sWP[32 * warp + (x >> 5)];
-          return x - (wv.y + __popc(wv.x & ((1u << (x & 31)) - 1u)));
-        };
-        uint32_t f = nvw;  // first input position of node wpf + lane
-        if (lane < span) {
-          uint32_t lo = 0, hi = nvw;
-          if (lane == 0) hi = 0;
-          while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if ((((uint32_t)sInS[seg + mid] & lmask) >> pshift) < wpf + lane) lo = mid + 1;
-            else hi = mid;
-          }
-          f = lo;
-        }
-        const uint32_t fnext = __shfl_down_sync(0xFFFFFFFFu, f, 1);
-        const uint32_t fe = lane + 1 < span ? fnext : nvw;
-        const uint32_t zs = zeros_before(f), ze = zeros_before(fe);
-        const uint2 tb = lane < span ? tab[wpf + lane] : make_uint2(0u, 0u);
-        const uint32_t gzq = tb.x + Zw + zs;         // destination of the node's zeros
-        const uint32_t goq = tb.y + Ow + (f - zs);   // destination of the node's ones
-        const uint32_t zrun = ze - zs, orun = (fe - ze) - (f - zs);
-        for (uint32_t q = 0; q < span; ++q) {
-#pragma unroll
-          for (uint32_t part = 0; part < 2; ++part) {
-            const uint32_t len = __shfl_sync(0xFFFFFFFFu, part ? orun : zrun, q);
-            if (len == 0) continue;
-            const uint32_t src = __shfl_sync(0xFFFFFFFFu, part ? nzw + (f - zs) : zs, q);
-            const uint32_t dst = __shfl_sync(0xFFFFFFFFu, part ? goq : gzq, q);
-            const uint32_t dt = dst >> a.log2T, bnd = (dt + 1) << a.log2T;
-            uint32_t ca = 0, cb = 0;
-            for (uint32_t e = lane; e < len; e += 32) {
-              const Sym v = stageS[src + e];
-              const uint32_t d = dst + e;
-              if (d < a.n) {
-                outS[d] = v;
-                const uint32_t one = ((uint32_t)v >> k1) & 1u;
-                if (d < bnd) ca += one;
-                else cb += one;
-              }
-            }
-            ca = __reduce_add_sync(0xFFFFFFFFu, ca);
-            cb = __reduce_add_sync(0xFFFFFFFFu, cb);
-            if (lane == 0) {
-              if (ca && dt < a.NT) counts_add(a.cout, dt, ca);
-              if (cb && dt + 1 < a.NT) counts_add(a.cout, dt + 1, cb);
-            }
+          if (SB > 1 && a.nones_next) {
+            if (v0 + v1) atomicAdd(&a.nones_next[2 * wpf], v0 + v1);
+            if (v2 + v3) atomicAdd(&a.nones_next[2 * wpf + 1], v2 + v3);
           }
         }
       } else {
-        // More than 32 nodes in the warp: each symbol goes to the zero or
-        // one range of its own node.  Zeros (then ones) are staged in node
-        // order, so their destinations rise monotonically: ones are counted
-        // per run of equal destination tile, carried across groups, one
-        // flush per change of tile.
-        Sym *outS = reinterpret_cast<Sym *>(a.out);
-        uint32_t cdt = 0xFFFFFFFFu, ccnt = 0;  // running destination tile and its ones
-        for (uint32_t base = 0; base < nvw; base += 32) {
-          const uint32_t kk = base + lane;
-          const bool valid = kk < nvw;
-          const Sym sv = valid ? stageS[kk] : (Sym)0;
-          const uint32_t p = ((uint32_t)sv & lmask) >> pshift;
-          const uint2 tb = valid ? tab[p] : make_uint2(0u, 0u);
-          uint32_t dt = 0xFFFFFFFFu, bit = 0;
-          if (valid) {
-            const uint32_t dest = kk < nzw ? tb.x + Zw + kk : tb.y + Ow + (kk - nzw);
-            if (dest < a.n) {
-              outS[dest] = sv;
-              dt = dest >> a.log2T;
-              bit = ((uint32_t)sv >> k1) & 1u;
-            }
-          }
-          const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit);
-          const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, dt, 1);
-          uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || dt != prev);
-          while (heads) {  // warp-uniform: one step per run of equal dt
-            const uint32_t h = __ffs(heads) - 1;
-            heads &= heads - 1;
-            const uint32_t sdt = __shfl_sync(0xFFFFFFFFu, dt, h);
-            if (sdt == 0xFFFFFFFFu) continue;
-            const uint32_t nx = heads ? (uint32_t)__ffs(heads) - 1 : 32u;
-            const uint32_t seg_mask = (nx == 32 ? 0xFFFFFFFFu : (1u << nx) - 1u) & ~((1u << h) - 1u);
-            const uint32_t c = __popc(ones & seg_mask);
-            if (sdt == cdt) {
-              ccnt += c;
-            } else {
-              if (lane == 0 && ccnt) counts_add(a.cout, cdt, ccnt);
-              cdt = sdt;
-              ccnt = c;
-            }
-          }
-        }
-        if (lane == 0 && ccnt) counts_add(a.cout, cdt, ccnt);
+        split_multi_node<SB>(a.out, a.n, a.log2T, a.NT, a.cout, a.nones_next, tab, sInS, stageS,
+                             sWP + 32 * warp, seg, nvw, nzw, wpf, wpl, Zw, Ow, lmask, pshift, k1);
       }
     }
     if (ring_slot) *ring_slot = ring_value;
@@ -937,6 +1035,27 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
     if (tid < 4 && one_node) {
       // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
       const uint32_t v = sm.cnt[tid];
+      if (SB > 1 && a.nones_next) {
+        // the zero run lies in child 2pf, the one run in child 2pf+1; a
+        // node spans many tiles at shallow levels, so thread 0 accumulates
+        // the current node's counts and flushes them when the node changes
+        const uint32_t pair = v + __shfl_down_sync(0xFu, v, 1);
+        const uint32_t p1 = __shfl_sync(0xFu, pair, 2);
+        if (tid == 0) {
+          if (sm.nc[0] == pf) {
+            sm.nc[1] += pair;
+            sm.nc[2] += p1;
+          } else {
+            if (sm.nc[0] != 0xFFFFFFFFu) {
+              if (sm.nc[1]) atomicAdd(&a.nones_next[2 * sm.nc[0]], sm.nc[1]);
+              if (sm.nc[2]) atomicAdd(&a.nones_next[2 * sm.nc[0] + 1], sm.nc[2]);
+            }
+            sm.nc[0] = pf;
+            sm.nc[1] = pair;
+            sm.nc[2] = p1;
+          }
+        }
+      }
       if (v) {
         sm.cnt[tid] = 0;
         const uint32_t dt = (sm.run[tid >> 1] >> a.log2T) + (tid & 1);
@@ -970,6 +1089,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_sp
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
   uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
   uint32_t *const sRun = sCnt + 4;                   // 2 run starts
+  uint32_t *const sNc = sRun + 2;                    // node-count cache (3 words)
   pipe.in = a.in;
   pipe.in_padded = a.in_padded;
   pipe.n = a.n;
@@ -981,19 +1101,25 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_sp
   const bool tab_smem = nodes <= kTabSmem;
   const uint2 *const tab = tab_smem ? sTab : a.tab;
 
-  if (a.matrix) {
-    // Wavelet matrix (Section 7): the whole level is one node; its ones go
+  if (a.count_table) {
+    // One node (the wavelet matrix of Section 7, or level 0): its ones go
     // after all zeros of the level, which are n minus the level's ones,
     // summed from the top tier of the level's tile counts.
     if (tid < 32) {
       const uint32_t ones = counts_total_warp(a.cin, a.NT);
-      if (tid == 0) sTab[0] = make_uint2(0u, a.n - ones);
+      if (tid == 0) {
+        sTab[0] = make_uint2(0u, a.n - ones);
+        if (a.tab_out && blockIdx.x == 0) a.tab_out[0] = sTab[0];
+      }
     }
   } else if (tab_smem) {
     for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
   }
   if (tid < 4) sCnt[tid] = 0;
-  if (tid == 0) pipe.prologue();
+  if (tid == 0) {
+    sNc[0] = 0xFFFFFFFFu;
+    pipe.prologue();
+  }
   __syncthreads();
   PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
 
@@ -1015,9 +1141,13 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_sp
     uint8_t *const sIn = pipe.data(it);
     if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
 
-    const SplitShared sm{sStage, sWP, sWT, sCnt, sRun};
+    const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc};
     split_tile<SB, THREADS>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
     pre = pre_next;
+  }
+  if (SB > 1 && a.nones_next && tid == 0 && sNc[0] != 0xFFFFFFFFu) {  // the cached node's counts
+    if (sNc[1]) atomicAdd(&a.nones_next[2 * sNc[0]], sNc[1]);
+    if (sNc[2]) atomicAdd(&a.nones_next[2 * sNc[0] + 1], sNc[2]);
   }
 }
 
@@ -1116,6 +1246,103 @@ __global__ void __launch_bounds__(kScanThreads) k_level_tables(TabArgs a) {
     const uint32_t p = base + i;
     if (p < cnt) tl[p] = make_uint2(O, (uint32_t)a.E[(uint64_t)(2 * p + 1) << sh] - O);
     O += c1[i];
+  }
+}
+
+struct NodeTabArgs {
+  const uint32_t *ones;    // ones of level m per node (2^m counters)
+  const uint2 *tab_prev;   // level m-1 table
+  uint2 *tab;              // level m table (null for the last level: node starts only)
+  unsigned long long *E;   // node starts, 2^L + 1 entries
+  uint32_t L, m, n, nblocks;
+  uint32_t *ticket;
+  Lookback lb;
+};
+
+// Node tables of level m from per-node counts (no histogram).  With
+// s(q) = start of node q of level m (= E[q << (L-m)]) and c(q) its ones:
+//   O_m(q) = sum of c over nodes < q            (exclusive scan, look-back)
+//   tab_m[q] = {O_m(q), s(q+1) - c(q) - O_m(q)}  (the 1-child of q starts at
+//               s(q+1) - c(q): the node's ones come last)
+// Node starts are not scanned: an even node starts where its parent does
+// (written at a coarser level), an odd node q where the parent's 1-child
+// does, tab_{m-1}[q/2].x + tab_{m-1}[q/2].y; the kernel writes
+// E[q << (L-m)] for odd q.  Level 1 also writes E[0] = 0 and E[2^L] = n.
+__global__ void __launch_bounds__(kScanThreads) k_node_tables(NodeTabArgs a) {
+  __shared__ uint32_t s_warp[33];
+  __shared__ uint32_t s_tile, s_P;
+  const uint32_t tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= a.nblocks) return;
+  const uint32_t cnt = 1u << a.m, sh = a.L - a.m;
+  const uint32_t base = tile * kScanChunk + tid * kScanItems;
+  auto start_of = [&](uint32_t q) -> uint32_t {  // s(q), 0 <= q <= 2^m
+    if (q >= cnt) return a.n;
+    if (q & 1u) {
+      const uint2 t = a.tab_prev[q >> 1];
+      return t.x + t.y;
+    }
+    return (uint32_t)a.E[(uint64_t)q << sh];
+  };
+  uint32_t c[kScanItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    c[i] = base + i < cnt ? __ldcg(&a.ones[base + i]) : 0u;
+    sum += c[i];
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<kScanThreads>(sum, s_warp, &total);
+  if (tid < 32) {
+    const uint32_t P = lookback(a.lb, tile, 0, total);
+    if (tid == 0) s_P = P;
+  }
+  __syncthreads();
+  uint32_t O = s_P + excl;
+#pragma unroll
+  for (int i = 0; i < (int)kScanItems; ++i) {
+    const uint32_t q = base + i;
+    if (q < cnt) {
+      if (q & 1u) a.E[(uint64_t)q << sh] = start_of(q);
+      if (a.tab) a.tab[q] = make_uint2(O, start_of(q + 1) - c[i] - O);
+    }
+    O += c[i];
+  }
+  if (a.m == 1 && tile == 0 && tid == 0) {
+    a.E[0] = 0;
+    a.E[1ull << a.L] = a.n;
+  }
+}
+
+struct LeafStartArgs {
+  const uint32_t *ones;   // ones of level L-1 per node
+  const uint2 *tab_prev;  // level L-2 table
+  unsigned long long *E;
+  uint32_t L, n;
+};
+
+// Node starts of the last two levels from per-node counts: node q of level
+// L-1 starts at E[2q] (odd q: where the 1-child of its parent starts), and
+// its 1-child, the symbol value 2q+1, at s(q+1) - c(q).
+__global__ void k_leaf_starts(LeafStartArgs a) {
+  const uint32_t cnt = 1u << (a.L - 1);
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+    uint32_t next;
+    if (q + 1 >= cnt) {
+      next = a.n;
+    } else if ((q + 1) & 1u) {
+      const uint2 t = a.tab_prev[(q + 1) >> 1];
+      next = t.x + t.y;
+    } else {
+      next = (uint32_t)a.E[2ull * (q + 1)];
+    }
+    if (q & 1u) {
+      const uint2 t = a.tab_prev[q >> 1];
+      a.E[2ull * q] = t.x + t.y;
+    }
+    a.E[2ull * q + 1] = next - __ldcg(&a.ones[q]);
   }
 }
 
