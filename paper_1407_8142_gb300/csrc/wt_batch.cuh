@@ -141,7 +141,7 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     const SplitShared sm{sStage, sWP, sWT, sMisc, sMisc + 4};
     if (tid < 4) sMisc[tid] = 0;
     __syncthreads();
-    split_tile<SB, THREADS>(a, a.tab, tile, sIn, pre.sum(), sm, nullptr, 0);
+    split_tile<SB, THREADS, false>(a, a.tab, tile, sIn, pre.sum(), sm, nullptr, 0);
   } else {
     LeafArgs a;
     a.in = L >= 2 ? tr.buf[(L - 2) & 1] : tr.in;

@@ -55,6 +55,8 @@ int cuda_fail(cudaError_t e) {
     }                                         \
   } while (0)
 
+constexpr uint64_t kNodeCountsMinN = 1ull << 24;
+
 uint32_t levels_of(uint32_t sigma) {
   uint32_t L = 0;
   while ((1ull << L) < sigma) ++L;
@@ -234,7 +236,7 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.ticket = ln.ticket();
   a.spin_limit = ln.spin();
   a.err = ln.err();
-  auto kern = k_split<SB, THREADS>;
+  auto kern = t->node_counts ? k_split<SB, THREADS, true> : k_split<SB, THREADS, false>;
   constexpr uint32_t sm = split_smem_bytes<SB, THREADS>();
   if (int rc = set_smem(kern, sm)) return rc;
   const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
@@ -415,9 +417,13 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   t->sb = symbol_bytes;
   t->L = L;
   t->shape = shape;
-  // large alphabets: per-node counts kept by the split passes replace the
-  // 2^L-bin histogram (whose global atomics serialise on hot symbols)
-  t->node_counts = shape == WT_SHAPE_TREE && (1ull << L) > kHistSmemMaxBins;
+  // per-node counts kept by the split passes replace the 2^L-bin histogram:
+  // for large alphabets (whose global histogram atomics serialise on hot
+  // symbols) and for long sequences (where the histogram's shared-memory
+  // atomics cost more than one small table kernel per level); short
+  // sequences with small alphabets keep the histogram (fewer launches)
+  t->node_counts = shape == WT_SHAPE_TREE && L >= 2 &&
+                   ((1ull << L) > kHistSmemMaxBins || n >= kNodeCountsMinN);
   t->NB = (n + 511) / 512;
   t->W = 16 * t->NB;
   t->threads = pick_threads(n, symbol_bytes, t->sms, t->cfg.tile_threads);

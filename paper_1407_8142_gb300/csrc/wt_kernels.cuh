@@ -644,11 +644,10 @@ constexpr uint32_t split_smem_bytes() {
 // one node either): each symbol goes to the zero or one range of its own
 // node.  wWP is the warp's {bit word, ones before the word} array.
 //   1-byte symbols: symbol by symbol (small alphabets have few multi-node
-//     warps, and this form keeps the single-node path's registers intact;
-//     node counts never apply, sigma <= 256).
+//     warps, and this form keeps the single-node path's registers intact).
 //   wider symbols, at most 32 nodes in the warp: one run per node and part.
 //   more nodes: symbol by symbol.
-template <int SB>
+template <int SB, bool NC>
 __device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint32_t log2T, uint32_t NT,
                                               TileCounts cout, uint32_t *nones_next, const uint2 *tab,
                                               const typename SymT<SB>::type *sInS,
@@ -666,7 +665,6 @@ __device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint3
     // per lane, and exchanged by shuffle.
     (void)sInS;
     (void)wWP;
-    (void)nones_next;
     Sym *outS = reinterpret_cast<Sym *>(out);
     const uint32_t span = wpl - wpf + 1;
     const bool lanes_tab = wpl >= wpf && span <= 32;
@@ -696,6 +694,12 @@ __device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint3
         }
       }
       const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit);
+      if (NC && nones_next) {  // ones of level l+1 per child node 2p + bit
+        const uint32_t child = dt != 0xFFFFFFFFu ? 2 * p + (kk >= nzw ? 1u : 0u) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, child);
+        const uint32_t c = __popc(ones & peers);
+        if (child != 0xFFFFFFFFu && c && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&nones_next[child], c);
+      }
       const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, dt, 1);
       uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || dt != prev);
       while (heads) {  // warp-uniform: one step per run of equal dt
@@ -772,7 +776,7 @@ __device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint3
         if (lane == 0) {
           if (ca && dt < NT) counts_add(cout, dt, ca);
           if (cb && dt + 1 < NT) counts_add(cout, dt + 1, cb);
-          if (nones_next && ca + cb) atomicAdd(&nones_next[2 * (wpf + q) + part], ca + cb);
+          if (NC && nones_next && ca + cb) atomicAdd(&nones_next[2 * (wpf + q) + part], ca + cb);
         }
       }
     }
@@ -800,7 +804,7 @@ __device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint3
         }
       }
       const uint32_t ones = __ballot_sync(0xFFFFFFFFu, bit);
-      if (nones_next) {  // ones of level l+1 per child node 2p + bit
+      if (NC && nones_next) {  // ones of level l+1 per child node 2p + bit
         const uint32_t child = dt != 0xFFFFFFFFu ? 2 * p + (kk >= nzw ? 1u : 0u) : 0xFFFFFFFFu;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, child);
         const uint32_t c = __popc(ones & peers);
@@ -845,7 +849,7 @@ struct SplitShared {
 // sIn holds the tile's symbols; share is this thread's part of the tile's
 // ones-prefix (summed over the block here).  Ends with a block barrier,
 // after which thread 0 has stored ring_value to *ring_slot (if non-null).
-template <int SB, int THREADS>
+template <int SB, int THREADS, bool NC>
 __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab, uint32_t tile,
                                            const uint8_t *sIn, uint32_t share_part,
                                            const SplitShared &sm, uint32_t *ring_slot,
@@ -1020,13 +1024,13 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
           if (v1 && t0 + 1 < a.NT) counts_add(a.cout, t0 + 1, v1);
           if (v2 && t1 < a.NT) counts_add(a.cout, t1, v2);
           if (v3 && t1 + 1 < a.NT) counts_add(a.cout, t1 + 1, v3);
-          if (SB > 1 && a.nones_next) {
+          if (NC && a.nones_next) {
             if (v0 + v1) atomicAdd(&a.nones_next[2 * wpf], v0 + v1);
             if (v2 + v3) atomicAdd(&a.nones_next[2 * wpf + 1], v2 + v3);
           }
         }
       } else {
-        split_multi_node<SB>(a.out, a.n, a.log2T, a.NT, a.cout, a.nones_next, tab, sInS, stageS,
+        split_multi_node<SB, NC>(a.out, a.n, a.log2T, a.NT, a.cout, a.nones_next, tab, sInS, stageS,
                              sWP + 32 * warp, seg, nvw, nzw, wpf, wpl, Zw, Ow, lmask, pshift, k1);
       }
     }
@@ -1035,13 +1039,15 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
     if (tid < 4 && one_node) {
       // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
       const uint32_t v = sm.cnt[tid];
-      if (SB > 1 && a.nones_next) {
+      if (NC && a.nones_next) {
         // the zero run lies in child 2pf, the one run in child 2pf+1; a
         // node spans many tiles at shallow levels, so thread 0 accumulates
         // the current node's counts and flushes them when the node changes
         const uint32_t pair = v + __shfl_down_sync(0xFu, v, 1);
         const uint32_t p1 = __shfl_sync(0xFu, pair, 2);
         if (tid == 0) {
+          // the tile's node, read again from the tile (still in shared memory)
+          const uint32_t pf = ((uint32_t)reinterpret_cast<const Sym *>(sIn)[0] & lmask) >> pshift;
           if (sm.nc[0] == pf) {
             sm.nc[1] += pair;
             sm.nc[2] += p1;
@@ -1073,7 +1079,10 @@ constexpr int split_min_blocks() {
   return (int)(by_smem < by_warps ? (by_smem ? by_smem : 1u) : by_warps);
 }
 
-template <int SB, int THREADS>
+// NC: the tree's node sizes come from node counts (a.nones_next set): the
+// pass also counts the next level's ones per child node.  Compiled as a
+// separate kernel so that the other builds carry none of that code.
+template <int SB, int THREADS, bool NC>
 __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_split(SplitArgs a) {
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t NW = THREADS / 32;
@@ -1142,10 +1151,10 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_sp
     if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
 
     const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc};
-    split_tile<SB, THREADS>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+    split_tile<SB, THREADS, NC>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
     pre = pre_next;
   }
-  if (SB > 1 && a.nones_next && tid == 0 && sNc[0] != 0xFFFFFFFFu) {  // the cached node's counts
+  if (NC && a.nones_next && tid == 0 && sNc[0] != 0xFFFFFFFFu) {  // the cached node's counts
     if (sNc[1]) atomicAdd(&a.nones_next[2 * sNc[0]], sNc[1]);
     if (sNc[2]) atomicAdd(&a.nones_next[2 * sNc[0] + 1], sNc[2]);
   }
@@ -1325,7 +1334,8 @@ struct LeafStartArgs {
 
 // Node starts of the last two levels from per-node counts: node q of level
 // L-1 starts at E[2q] (odd q: where the 1-child of its parent starts), and
-// its 1-child, the symbol value 2q+1, at s(q+1) - c(q).
+// its 1-child, the symbol value 2q+1, at s(q+1) - c(q).  Also E[0] = 0 and
+// E[2^L] = n.
 __global__ void k_leaf_starts(LeafStartArgs a) {
   const uint32_t cnt = 1u << (a.L - 1);
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
@@ -1343,6 +1353,10 @@ __global__ void k_leaf_starts(LeafStartArgs a) {
       a.E[2ull * q] = t.x + t.y;
     }
     a.E[2ull * q + 1] = next - __ldcg(&a.ones[q]);
+    if (q == 0) {  // the ends (also written at level 1 when there are more levels)
+      a.E[0] = 0;
+      a.E[1ull << a.L] = a.n;
+    }
   }
 }
 
