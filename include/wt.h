@@ -147,9 +147,12 @@ int wt_build_ex(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_b
 /*
  * Host-memory path: copy h_seq[0..n) to the device, build, and copy the
  * bitmaps (L*W uint32) into h_bits and the directory (L*(NB+1) uint64) into
- * h_rank (either may be NULL to skip that copy).  Synchronises `stream`
- * before returning and returns the build status (as wt_sync).
- * The tree must have been created for this n, sigma and symbol_bytes.
+ * h_rank (either may be NULL to skip that copy).  Each level's rows are
+ * copied on a stream of the tree's own as soon as the pass that writes them
+ * has finished, overlapping the copies with the later passes (page-locked
+ * host buffers make the copies asynchronous).  Synchronises before
+ * returning and returns the build status (as wt_sync).  The tree must have
+ * been created for this n, sigma and symbol_bytes; not for views.
  */
 int wt_build_host(wt_tree *tree, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
                   void *stream);

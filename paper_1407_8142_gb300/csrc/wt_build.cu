@@ -234,8 +234,10 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.ticket = ln.ticket();
   a.spin_limit = ln.spin();
   a.err = ln.err();
-  auto kern = t->node_counts ? k_split<SB, THREADS, true> : k_split<SB, THREADS, false>;
-  constexpr uint32_t sm = split_smem_bytes<SB, THREADS>();
+  // 4-byte symbols: one input buffer (see TilePipe), more CTAs per SM
+  constexpr int DEPTH = SB == 4 ? 1 : 2;
+  auto kern = t->node_counts ? k_split<SB, THREADS, true, DEPTH> : k_split<SB, THREADS, false, DEPTH>;
+  constexpr uint32_t sm = split_smem_bytes<SB, THREADS, DEPTH>();
   if (int rc = set_smem(kern, sm)) return rc;
   const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
   ln.before(kSplit);
@@ -332,11 +334,14 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
     if (t->node_counts && l >= 1 && (rc = launch_node_tables(ln, l))) return rc;
     uint8_t *out = static_cast<uint8_t *>(t->d_buf[l & 1]);
     if ((rc = launch_split<SB, THREADS>(ln, in, padded, out, l))) return rc;
+    if (t->record_levels) WT_CUDA(cudaEventRecord(t->level_ev[l], st));  // level l's rows are final
     in = out;
     padded = true;
   }
   if (t->node_counts && (rc = launch_node_tables(ln, t->L - 1))) return rc;
-  return launch_leaf<SB, THREADS>(ln, in, padded, t->L - 1);
+  if ((rc = launch_leaf<SB, THREADS>(ln, in, padded, t->L - 1))) return rc;
+  if (t->record_levels) WT_CUDA(cudaEventRecord(t->level_ev[t->L - 1], st));
+  return WT_OK;
 }
 
 template <int SB>
@@ -360,6 +365,12 @@ void release(wt_tree *t) {
   cudaFree(t->d_buf[1]);
   cudaFree(t->d_status);
   cudaFree(t->d_in_host);
+  if (t->copy_stream) {
+    cudaStreamSynchronize(t->copy_stream);
+    cudaStreamDestroy(t->copy_stream);
+    for (uint32_t l = 0; l < kMaxLevels; ++l)
+      if (t->level_ev[l]) cudaEventDestroy(t->level_ev[l]);
+  }
   if (t->ev) {
     for (uint32_t i = 0; i < 2 * kMaxProfiled; ++i)
       if (t->ev[i]) cudaEventDestroy(t->ev[i]);
@@ -552,17 +563,34 @@ int wt_sync(wt_tree *t) {
 
 int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
                   void *stream) {
-  if (!t || (!h_seq && t->n)) return WT_ERR_ARG;
+  if (!t || (!h_seq && t->n) || t->owner) return WT_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->NT * t->T * t->sb + 16));
+  const uint32_t L = t->L;
+  const bool copy_out = t->n && L && (h_bits || h_rank);
+  if (copy_out && !t->copy_stream) {
+    WT_CUDA(cudaStreamCreateWithFlags(&t->copy_stream, cudaStreamNonBlocking));
+    for (uint32_t l = 0; l < L; ++l) WT_CUDA(cudaEventCreateWithFlags(&t->level_ev[l], cudaEventDisableTiming));
+  }
   if (t->n) WT_CUDA(cudaMemcpyAsync(t->d_in_host, h_seq, t->n * t->sb, cudaMemcpyHostToDevice, st));
+  // each level's bitmap and directory rows are copied out while the later
+  // levels are still being built
+  t->record_levels = copy_out;
   int rc = wt_rebuild(t, t->d_in_host, stream);
+  t->record_levels = false;
   if (rc) return rc;
-  const uint32_t Lz = t->L;
-  if (h_bits && Lz && t->W)
-    WT_CUDA(cudaMemcpyAsync(h_bits, t->d_bits, (size_t)Lz * t->W * 4, cudaMemcpyDeviceToHost, st));
-  if (h_rank && Lz)
-    WT_CUDA(cudaMemcpyAsync(h_rank, t->d_rank, (size_t)Lz * (t->NB + 1) * 8, cudaMemcpyDeviceToHost, st));
+  if (copy_out) {
+    for (uint32_t l = 0; l < L; ++l) {
+      WT_CUDA(cudaStreamWaitEvent(t->copy_stream, t->level_ev[l], 0));
+      if (h_bits && t->W)
+        WT_CUDA(cudaMemcpyAsync(h_bits + (uint64_t)l * t->W, t->d_bits + (uint64_t)l * t->W, t->W * 4,
+                                cudaMemcpyDeviceToHost, t->copy_stream));
+      if (h_rank)
+        WT_CUDA(cudaMemcpyAsync(h_rank + (uint64_t)l * (t->NB + 1), t->d_rank + (uint64_t)l * (t->NB + 1),
+                                (t->NB + 1) * 8, cudaMemcpyDeviceToHost, t->copy_stream));
+    }
+    WT_CUDA(cudaStreamSynchronize(t->copy_stream));
+  }
   return wt_sync(t);
 }
 

@@ -61,6 +61,12 @@ struct wt_tree {
   uint64_t sel_stride = 0;        // entries per (level, bit value)
   uint32_t sel_for = 0;           // build_count + 1 the index was built for (0 = none)
 
+  // host-buffer builds: each level's rows are copied out on copy_stream as
+  // soon as the pass that writes them is done (level_ev, recorded after it)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t level_ev[wtk::kMaxLevels] = {};
+  bool record_levels = false;
+
   bool profile = false;
   cudaEvent_t *ev = nullptr;      // 2 * kMaxProfiled events, created on first use
   int32_t *ev_kind = nullptr;

@@ -90,7 +90,11 @@ __device__ __forceinline__ void write_level(const LevelOut &o, uint32_t tile, ui
 // are copied into shared memory by the TMA engine one tile ahead (double
 // buffer), and the loads of a tile's count prefix are issued one tile ahead,
 // so no round trip to memory sits between two tiles of a CTA.
-template <int SB, int THREADS>
+// DEPTH 2: the copy of tile it+1 runs while tile it is processed (double
+// buffer).  DEPTH 1: one buffer, the next tile is copied once the current one
+// is done; the shared memory saved lets more CTAs share an SM, and their
+// work covers the copy.
+template <int SB, int THREADS, int DEPTH = 2>
 struct TilePipe {
   static constexpr uint32_t T = 32 * THREADS;
   static constexpr uint32_t TB = T * SB;
@@ -125,24 +129,37 @@ struct TilePipe {
   // tile it+1
   __device__ __forceinline__ uint32_t advance(uint32_t it, uint32_t nxt) const {
     const uint32_t nn = atomicAdd(ticket, 1u);
-    if (nxt < NT) {
+    if (DEPTH == 2 && nxt < NT) {
       fence_proxy_async_smem();
       issue(nxt, (it + 1) & 1);
     }
     return nn;
   }
+  // DEPTH 1, thread 0 after the block barrier that ends tile it: start the
+  // copy of tile it+1 into the (now free) buffer
+  __device__ __forceinline__ void after_tile(uint32_t nxt) const {
+    if (DEPTH == 1 && nxt < NT) {
+      fence_proxy_async_smem();
+      issue(nxt, 0);
+    }
+  }
   // all threads: wait for tile `it`'s symbols (bounded); false on timeout
   __device__ __forceinline__ bool wait(uint32_t it, uint32_t spin, int *err) const {
+    if (DEPTH == 1) return mbar_wait_bounded(&bar[0], it & 1u, spin, err);
     return mbar_wait_bounded(&bar[it & 1], (it >> 1) & 1u, spin, err);
   }
   // after a timeout: wait (bounded) for the copies this CTA started
   __device__ __forceinline__ void drain(uint32_t it, uint32_t spin, int *err) const {
     if (threadIdx.x == 0) {
+      if (DEPTH == 1) {
+        mbar_wait_bounded(&bar[0], it & 1u, spin, err);
+        return;
+      }
       mbar_wait_bounded(&bar[it & 1], (it >> 1) & 1u, spin, err);
       if (ring[(it + 1) % 3] < NT) mbar_wait_bounded(&bar[(it + 1) & 1], ((it + 1) >> 1) & 1u, spin, err);
     }
   }
-  __device__ __forceinline__ uint8_t *data(uint32_t it) const { return (it & 1) ? sIn1 : sIn0; }
+  __device__ __forceinline__ uint8_t *data(uint32_t it) const { return (DEPTH == 2 && (it & 1)) ? sIn1 : sIn0; }
   // tail bytes of an unpadded input that the bulk copy (multiple of 16 bytes) left out
   __device__ __forceinline__ bool fill_tail(uint8_t *sIn, uint64_t start, uint32_t nv) const {
     if (in_padded || ((nv * SB) & 15u) == 0) return false;
@@ -631,12 +648,12 @@ __host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * SB + 48u; 
 
 constexpr uint32_t kTabSmem = 1024;  // level tables up to this many nodes live in shared memory
 
-template <int SB, int THREADS>
+template <int SB, int THREADS, int DEPTH = 2>
 constexpr uint32_t split_smem_bytes() {
-  // two input tiles, per-warp staging, per-thread {bit word, warp-local
+  // DEPTH input tiles, per-warp staging, per-thread {bit word, warp-local
   // ones-prefix}, per-warp {ones, prefix share}, the level table, mbarriers,
   // tickets, run counters and run starts
-  return pipe_smem_bytes<SB, THREADS>() + (THREADS / 32) * stage_bytes<SB>() + 8u * THREADS +
+  return DEPTH * 32u * THREADS * SB + (THREADS / 32) * stage_bytes<SB>() + 8u * THREADS +
          8u * (THREADS / 32) + 8u * kTabSmem + 192u;
 }
 
@@ -1072,9 +1089,9 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
 
 // Resident CTAs per SM the split pass is compiled for: as many as shared
 // memory allows, up to 48 warps per SM (caps registers at 42 per thread).
-template <int SB, int THREADS>
+template <int SB, int THREADS, int DEPTH = 2>
 constexpr int split_min_blocks() {
-  constexpr uint32_t by_smem = 232448u / split_smem_bytes<SB, THREADS>();
+  constexpr uint32_t by_smem = 232448u / split_smem_bytes<SB, THREADS, DEPTH>();
   constexpr uint32_t by_warps = 1536u / THREADS;
   return (int)(by_smem < by_warps ? (by_smem ? by_smem : 1u) : by_warps);
 }
@@ -1082,15 +1099,15 @@ constexpr int split_min_blocks() {
 // NC: the tree's node sizes come from node counts (a.nones_next set): the
 // pass also counts the next level's ones per child node.  Compiled as a
 // separate kernel so that the other builds carry none of that code.
-template <int SB, int THREADS, bool NC>
-__global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_split(SplitArgs a) {
+template <int SB, int THREADS, bool NC, int DEPTH>
+__global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH>()) k_split(SplitArgs a) {
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t NW = THREADS / 32;
   extern __shared__ __align__(128) uint8_t smem[];
-  TilePipe<SB, THREADS> pipe;
+  TilePipe<SB, THREADS, DEPTH> pipe;
   pipe.sIn0 = smem;
-  pipe.sIn1 = smem + pipe.TB;
-  uint8_t *const sStage = smem + 2 * pipe.TB;
+  pipe.sIn1 = smem + (DEPTH - 1) * pipe.TB;
+  uint8_t *const sStage = smem + DEPTH * pipe.TB;
   uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());  // {word, prefix}
   uint2 *const sWT = sWP + THREADS;                  // per warp {ones, prefix share}
   uint2 *const sTab = sWT + NW;                      // level table (small levels)
@@ -1152,6 +1169,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS>()) k_sp
 
     const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc};
     split_tile<SB, THREADS, NC>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+    if (DEPTH == 1 && tid == 0) pipe.after_tile(nxt);
     pre = pre_next;
   }
   if (NC && a.nones_next && tid == 0 && sNc[0] != 0xFFFFFFFFu) {  // the cached node's counts
