@@ -75,10 +75,12 @@ def test_patterns_uint8(wt, kind, sigma):
     compare(wt, S, sigma)
 
 
-@pytest.mark.parametrize("sigma,b", [(1000, 2), (65536, 2), (7, 2), (5, 4), (70000, 4),
-                                     (1 << 20, 4), ((1 << 20) + 3, 4), (1 << 24, 4)])
+@pytest.mark.parametrize("sigma,b", [(1000, 2), (8192, 2), (8193, 2), (16384, 2), (65536, 2), (7, 2), (5, 4),
+                                     (70000, 4), (1 << 20, 4), ((1 << 20) + 3, 4), (1 << 24, 4)])
 @pytest.mark.parametrize("kind", ["uniform", "zipf", "sorted"])
 def test_wide_symbols(wt, sigma, b, kind):
+    """Covers both ways of finding node sizes: the shared-memory histogram
+    (sigma <= 8192) and per-node counts kept by the split passes (above)."""
     n = 40000 + 123
     S = synth.pattern(kind, n, sigma, b, seed=sigma % 97)
     compare(wt, S, sigma)
