@@ -234,14 +234,18 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.ticket = ln.ticket();
   a.spin_limit = ln.spin();
   a.err = ln.err();
-  // 4-byte symbols: one input buffer (see TilePipe), more CTAs per SM
+  // 4-byte symbols: one input buffer (see TilePipe), more CTAs per SM.
+  // 1-byte symbols in tiles of 16384: 256 threads of 64 symbols each, so
+  // that every warp's fixed per-tile work is spread over 2048 symbols.
   constexpr int DEPTH = SB == 4 ? 1 : 2;
-  auto kern = t->node_counts ? k_split<SB, THREADS, true, DEPTH> : k_split<SB, THREADS, false, DEPTH>;
-  constexpr uint32_t sm = split_smem_bytes<SB, THREADS, DEPTH>();
+  constexpr int WPT = (SB == 1 && THREADS == 512) ? 2 : 1;
+  constexpr int CTA = THREADS / WPT;
+  auto kern = t->node_counts ? k_split<SB, CTA, true, DEPTH, WPT> : k_split<SB, CTA, false, DEPTH, WPT>;
+  constexpr uint32_t sm = split_smem_bytes<SB, CTA, DEPTH, WPT>();
   if (int rc = set_smem(kern, sm)) return rc;
-  const int grid = std::min<int>((int)t->NT, occupancy(kern, THREADS, sm, t->sms, t->cfg.ctas_per_sm));
+  const int grid = std::min<int>((int)t->NT, occupancy(kern, CTA, sm, t->sms, t->cfg.ctas_per_sm));
   ln.before(kSplit);
-  kern<<<std::max(grid, 1), THREADS, sm, ln.st>>>(a);
+  kern<<<std::max(grid, 1), CTA, sm, ln.st>>>(a);
   ln.after();
   ++ln.pass;
   WT_CUDA(cudaGetLastError());

@@ -94,9 +94,9 @@ __device__ __forceinline__ void write_level(const LevelOut &o, uint32_t tile, ui
 // buffer).  DEPTH 1: one buffer, the next tile is copied once the current one
 // is done; the shared memory saved lets more CTAs share an SM, and their
 // work covers the copy.
-template <int SB, int THREADS, int DEPTH = 2>
+template <int SB, int THREADS, int DEPTH = 2, int WPT = 1>
 struct TilePipe {
-  static constexpr uint32_t T = 32 * THREADS;
+  static constexpr uint32_t T = 32 * WPT * THREADS;
   static constexpr uint32_t TB = T * SB;
   uint8_t *sIn0, *sIn1;
   uint64_t *bar;       // 2 mbarriers
@@ -643,17 +643,17 @@ __device__ __forceinline__ void scatter_one(uint32_t bit, uint32_t &oa, uint32_t
 
 // per-warp staging: 1024 symbols plus room to align both runs to their
 // global 16-byte phase
-template <int SB>
-__host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * SB + 48u; }
+template <int SB, int WPT = 1>
+__host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * WPT * SB + 48u; }
 
 constexpr uint32_t kTabSmem = 1024;  // level tables up to this many nodes live in shared memory
 
-template <int SB, int THREADS, int DEPTH = 2>
+template <int SB, int THREADS, int DEPTH = 2, int WPT = 1>
 constexpr uint32_t split_smem_bytes() {
-  // DEPTH input tiles, per-warp staging, per-thread {bit word, warp-local
+  // DEPTH input tiles, per-warp staging, per-word {bit word, warp-local
   // ones-prefix}, per-warp {ones, prefix share}, the level table, mbarriers,
   // tickets, run counters and run starts
-  return DEPTH * 32u * THREADS * SB + (THREADS / 32) * stage_bytes<SB>() + 8u * THREADS +
+  return DEPTH * 32u * WPT * THREADS * SB + (THREADS / 32) * stage_bytes<SB, WPT>() + 8u * WPT * THREADS +
          8u * (THREADS / 32) + 8u * kTabSmem + 192u;
 }
 
@@ -866,20 +866,24 @@ struct SplitShared {
 // sIn holds the tile's symbols; share is this thread's part of the tile's
 // ones-prefix (summed over the block here).  Ends with a block barrier,
 // after which thread 0 has stored ring_value to *ring_slot (if non-null).
-template <int SB, int THREADS, bool NC>
+// WPT: words (of 32 symbols) per thread; a warp's segment is 1024 * WPT
+// symbols (WPT > 1 only for 1-byte symbols).
+template <int SB, int THREADS, bool NC, int WPT = 1>
 __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab, uint32_t tile,
                                            const uint8_t *sIn, uint32_t share_part,
                                            const SplitShared &sm, uint32_t *ring_slot,
                                            uint32_t ring_value) {
+  static_assert(WPT == 1 || SB == 1, "several words per thread only for 1-byte symbols");
   using Sym = typename SymT<SB>::type;
-  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t T = 32 * WPT * THREADS;
+  constexpr uint32_t SPW = 1024 * WPT;  // symbols per warp
   constexpr uint32_t NW = THREADS / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t k = a.L - 1 - a.level;   // bit of this level
   const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
   const uint32_t pshift = a.pshift;       // node prefix = symbol >> pshift
   const uint32_t lmask = (1u << a.L) - 1u;
-  uint8_t *const stage = sm.stage + warp * stage_bytes<SB>();
+  uint8_t *const stage = sm.stage + warp * stage_bytes<SB, WPT>();
   Sym *const stageS = reinterpret_cast<Sym *>(stage);
   uint2 *const sWP = sm.wp;
   uint2 *const sWT = sm.wt;
@@ -888,19 +892,28 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
   const uint64_t start = (uint64_t)tile * T;
   const uint32_t nv = (uint32_t)umin64(T, a.n - start);
 
-    // Pass A: 32 consecutive symbols per thread -> one bitmap word; warp scan
-    // of the ones.
-    const uint32_t my0 = 32 * tid;
-    const uint32_t word = tile_word<SB, THREADS>(sIn, my0, k) & valid_mask(my0, nv);
-    const uint32_t pc = __popc(word);
+    // Pass A: 32 * WPT consecutive symbols per thread -> WPT bitmap words;
+    // warp scan of the ones.
+    const uint32_t my0 = 32 * WPT * tid;
+    uint32_t word[WPT];
+    uint32_t pc = 0;
+#pragma unroll
+    for (int i = 0; i < WPT; ++i) {
+      word[i] = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k) & valid_mask(my0 + 32 * i, nv);
+      pc += __popc(word[i]);
+    }
     uint32_t incl = pc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
       if (lane >= (uint32_t)o) incl += y;
     }
-    const uint32_t pw = incl - pc;  // ones before this word, within the warp
-    sWP[tid] = make_uint2(word, pw);
+    uint32_t pw[WPT];  // ones before each word, within the warp
+    pw[0] = incl - pc;
+#pragma unroll
+    for (int i = 1; i < WPT; ++i) pw[i] = pw[i - 1] + __popc(word[i - 1]);
+#pragma unroll
+    for (int i = 0; i < WPT; ++i) sWP[WPT * tid + i] = make_uint2(word[i], pw[i]);
     const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, share_part);
     if (lane == 31) sWT[warp] = make_uint2(incl, share);
     __syncthreads();
@@ -908,7 +921,20 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
     const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);  // ones before the warp
     const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
     const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);                       // ones before the tile
-    write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + pw, total);
+    if (WPT == 1) {
+      write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word[0], R, Pw + pw[0], total);
+    } else {
+#pragma unroll
+      for (int i = 0; i < WPT; ++i) {
+        const uint64_t widx = (uint64_t)tile * (WPT * THREADS) + WPT * tid + i;
+        if (widx < a.W) a.lo.bits[widx] = word[i];
+        if ((widx & 15) == 0 && start + my0 + 32 * i < a.n) a.lo.rank[(start + my0 + 32 * i) >> 9] = R + Pw + pw[i];
+      }
+      if (tile == a.NT - 1 && tid == 0) {
+        a.lo.rank[a.NB] = R + total;
+        *a.lo.zeros = (unsigned long long)(a.n - (R + total));
+      }
+    }
 
     // Pass B: stable split of the warp's segment into its staging area,
     // zeros first.  In step s lane i holds the G symbols at 32*G*s + G*i
@@ -917,8 +943,8 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
     // lies in one node, each run is staged at the 16-byte phase of its
     // destination in T_{l+1}, so that it is written with aligned 16-byte
     // copies.
-    const uint32_t seg = 1024 * warp;
-    const uint32_t nvw = nv > seg ? min(nv - seg, 1024u) : 0u;  // symbols of this warp
+    const uint32_t seg = SPW * warp;
+    const uint32_t nvw = nv > seg ? min(nv - seg, SPW) : 0u;    // symbols of this warp
     const uint32_t tw = __shfl_sync(0xFFFFFFFFu, incl, 31);
     const uint32_t nzw = nvw - tw;                              // zeros of this warp
     const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
@@ -952,15 +978,15 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
       const uint8_t *segIn = sIn + seg * SB;
       Sym *const zS = reinterpret_cast<Sym *>(stage + zoff);
       Sym *const oS = reinterpret_cast<Sym *>(stage + ooff);
-      if (nvw == 1024) {
+      if (nvw == SPW) {
         // Each symbol goes to the running zero or one pointer of its lane:
         // one predicate, two predicated stores, two predicated increments --
         // no branch, whatever the bits.
         const uint32_t zbase = smem_addr(zS), obase = smem_addr(oS);
 #pragma unroll 2
-        for (uint32_t s = 0; s < 32 / G8; ++s) {
+        for (uint32_t s = 0; s < 32 * WPT / G8; ++s) {
           const uint32_t pos0 = 32 * G8 * s + G8 * lane;
-          const uint2 wp = sWP[32 * warp + G8 * s + wsub];
+          const uint2 wp = sWP[32 * WPT * warp + G8 * s + wsub];
           const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
           const uint32_t bits = wp.x >> bo;
           const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the warp
@@ -973,9 +999,9 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
           }
         }
       } else {
-        for (uint32_t s = 0; s < 32 / G8; ++s) {
+        for (uint32_t s = 0; s < 32 * WPT / G8; ++s) {
           const uint32_t pos0 = 32 * G8 * s + G8 * lane;
-          const uint2 wp = sWP[32 * warp + G8 * s + wsub];
+          const uint2 wp = sWP[32 * WPT * warp + G8 * s + wsub];
           const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0 * SB);
           const uint32_t bits = wp.x >> bo;
           const uint32_t Rl = wp.y + __popc(wp.x & lowmask);
@@ -1048,7 +1074,7 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
         }
       } else {
         split_multi_node<SB, NC>(a.out, a.n, a.log2T, a.NT, a.cout, a.nones_next, tab, sInS, stageS,
-                             sWP + 32 * warp, seg, nvw, nzw, wpf, wpl, Zw, Ow, lmask, pshift, k1);
+                                 sWP + 32 * WPT * warp, seg, nvw, nzw, wpf, wpl, Zw, Ow, lmask, pshift, k1);
       }
     }
     if (ring_slot) *ring_slot = ring_value;
@@ -1089,9 +1115,9 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
 
 // Resident CTAs per SM the split pass is compiled for: as many as shared
 // memory allows, up to 48 warps per SM (caps registers at 42 per thread).
-template <int SB, int THREADS, int DEPTH = 2>
+template <int SB, int THREADS, int DEPTH = 2, int WPT = 1>
 constexpr int split_min_blocks() {
-  constexpr uint32_t by_smem = 232448u / split_smem_bytes<SB, THREADS, DEPTH>();
+  constexpr uint32_t by_smem = 232448u / split_smem_bytes<SB, THREADS, DEPTH, WPT>();
   constexpr uint32_t by_warps = 1536u / THREADS;
   return (int)(by_smem < by_warps ? (by_smem ? by_smem : 1u) : by_warps);
 }
@@ -1099,17 +1125,17 @@ constexpr int split_min_blocks() {
 // NC: the tree's node sizes come from node counts (a.nones_next set): the
 // pass also counts the next level's ones per child node.  Compiled as a
 // separate kernel so that the other builds carry none of that code.
-template <int SB, int THREADS, bool NC, int DEPTH>
-__global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH>()) k_split(SplitArgs a) {
-  constexpr uint32_t T = 32 * THREADS;
+template <int SB, int THREADS, bool NC, int DEPTH, int WPT = 1>
+__global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, WPT>()) k_split(SplitArgs a) {
+  constexpr uint32_t T = 32 * WPT * THREADS;
   constexpr uint32_t NW = THREADS / 32;
   extern __shared__ __align__(128) uint8_t smem[];
-  TilePipe<SB, THREADS, DEPTH> pipe;
+  TilePipe<SB, THREADS, DEPTH, WPT> pipe;
   pipe.sIn0 = smem;
   pipe.sIn1 = smem + (DEPTH - 1) * pipe.TB;
   uint8_t *const sStage = smem + DEPTH * pipe.TB;
-  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB>());  // {word, prefix}
-  uint2 *const sWT = sWP + THREADS;                  // per warp {ones, prefix share}
+  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB, WPT>());  // {word, prefix}
+  uint2 *const sWT = sWP + WPT * THREADS;            // per warp {ones, prefix share}
   uint2 *const sTab = sWT + NW;                      // level table (small levels)
   pipe.bar = reinterpret_cast<uint64_t *>(sTab + kTabSmem);
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
@@ -1168,7 +1194,8 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH>(
     if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
 
     const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc};
-    split_tile<SB, THREADS, NC>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+    split_tile<SB, THREADS, NC, WPT>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr,
+                                     nn);
     if (DEPTH == 1 && tid == 0) pipe.after_tile(nxt);
     pre = pre_next;
   }
