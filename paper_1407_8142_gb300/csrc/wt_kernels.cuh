@@ -646,7 +646,10 @@ __device__ __forceinline__ void scatter_one(uint32_t bit, uint32_t &oa, uint32_t
 template <int SB, int WPT = 1>
 __host__ __device__ constexpr uint32_t stage_bytes() { return 1024u * WPT * SB + 48u; }
 
-constexpr uint32_t kTabSmem = 1024;  // level tables up to this many nodes live in shared memory
+// Level tables of up to this many nodes live in shared memory.  1-byte
+// symbols have at most 2^7 nodes per split level (sigma <= 256).
+template <int SB>
+__host__ __device__ constexpr uint32_t tab_smem_nodes() { return SB == 1 ? 128u : 1024u; }
 
 template <int SB, int THREADS, int DEPTH = 2, int WPT = 1>
 constexpr uint32_t split_smem_bytes() {
@@ -654,7 +657,7 @@ constexpr uint32_t split_smem_bytes() {
   // ones-prefix}, per-warp {ones, prefix share}, the level table, mbarriers,
   // tickets, run counters and run starts
   return DEPTH * 32u * WPT * THREADS * SB + (THREADS / 32) * stage_bytes<SB, WPT>() + 8u * WPT * THREADS +
-         8u * (THREADS / 32) + 8u * kTabSmem + 192u;
+         8u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 192u;
 }
 
 // Phase C of a warp whose symbols span several nodes (the tile is not in
@@ -1114,12 +1117,17 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
 }
 
 // Resident CTAs per SM the split pass is compiled for: as many as shared
-// memory allows, up to 48 warps per SM (caps registers at 42 per thread).
+// memory allows, up to 48 warps per SM, but not so many that a thread gets
+// fewer than 48 registers (below that the pass spills) -- except with
+// 512-thread CTAs, where 3 per SM at 40 registers beat 2 at 64.
 template <int SB, int THREADS, int DEPTH = 2, int WPT = 1>
 constexpr int split_min_blocks() {
   constexpr uint32_t by_smem = 232448u / split_smem_bytes<SB, THREADS, DEPTH, WPT>();
   constexpr uint32_t by_warps = 1536u / THREADS;
-  return (int)(by_smem < by_warps ? (by_smem ? by_smem : 1u) : by_warps);
+  constexpr uint32_t by_regs = THREADS >= 512 ? by_warps : 65536u / (48u * THREADS);
+  constexpr uint32_t m = by_smem < by_warps ? by_smem : by_warps;
+  constexpr uint32_t r = m < by_regs ? m : by_regs;
+  return (int)(r ? r : 1u);
 }
 
 // NC: the tree's node sizes come from node counts (a.nones_next set): the
@@ -1137,7 +1145,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
   uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB, WPT>());  // {word, prefix}
   uint2 *const sWT = sWP + WPT * THREADS;            // per warp {ones, prefix share}
   uint2 *const sTab = sWT + NW;                      // level table (small levels)
-  pipe.bar = reinterpret_cast<uint64_t *>(sTab + kTabSmem);
+  pipe.bar = reinterpret_cast<uint64_t *>(sTab + tab_smem_nodes<SB>());
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
   uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
   uint32_t *const sRun = sCnt + 4;                   // 2 run starts
@@ -1150,7 +1158,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
 
   const uint32_t tid = threadIdx.x;
   const uint32_t nodes = 1u << (a.L - a.pshift);
-  const bool tab_smem = nodes <= kTabSmem;
+  const bool tab_smem = nodes <= tab_smem_nodes<SB>();
   const uint2 *const tab = tab_smem ? sTab : a.tab;
 
   if (a.count_table) {
