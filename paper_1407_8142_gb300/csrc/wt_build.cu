@@ -430,11 +430,13 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   t->sb = symbol_bytes;
   t->L = L;
   t->shape = shape;
-  // large alphabets: per-node counts kept by the split passes replace the
-  // 2^L-bin histogram, whose global atomics serialise on hot symbols.  (For
-  // 1-byte symbols the counting costs the split pass more than the shared-
-  // memory histogram costs the pre-pass.)
-  t->node_counts = shape == WT_SHAPE_TREE && (1ull << L) > kHistSmemMaxBins;
+  // per-node counts kept by the split passes replace the 2^L-bin histogram:
+  // for large alphabets, whose global histogram atomics serialise on hot
+  // symbols, and for long sequences, where the histogram's shared-memory
+  // atomics cost the pre-pass more than one small table kernel per level
+  // costs; short sequences of small alphabets keep it (fewer launches)
+  t->node_counts = shape == WT_SHAPE_TREE && L >= 2 &&
+                   ((1ull << L) > kHistSmemMaxBins || n >= (1ull << 24));
   t->NB = (n + 511) / 512;
   t->W = 16 * t->NB;
   t->threads = pick_threads(n, symbol_bytes, t->sms, t->cfg.tile_threads);

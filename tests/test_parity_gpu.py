@@ -217,6 +217,14 @@ def test_queries_at_scale(wt, shape, sigma, b):
             assert np.array_equal(t.select(c, k).cpu().numpy().view(np.uint64), s_ref)
 
 
+@pytest.mark.parametrize("sigma,kind", [(256, "zipf"), (5, "uniform"), (2, "uniform"), (256, "runs")])
+def test_long_small_alphabet(wt, sigma, kind):
+    """n >= 2^24 with 1-byte symbols: the node sizes come from node counts
+    (not the histogram) and the split pass runs 64 symbols per thread."""
+    S = synth.pattern(kind, (1 << 24) + 4097, sigma, 1, seed=sigma)
+    compare(wt, S, sigma)
+
+
 def test_config1_full(wt):
     """n = 2^20 uint8, uniform over 256 symbols, seed 0: the whole output."""
     S, sigma = synth.config1(0)
