@@ -191,11 +191,22 @@ def profiled_traffic():
     return float(m_bytes.group(1))
 
 
-def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int) -> float:
-    """Bytes the method must move for one launch (reads + writes)."""
+def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int, k: int = 1) -> float:
+    """Bytes the method must move for one launch (reads + writes).  For the
+    k-level schedule, level_index is the pass index: pass j covers levels
+    j*k .. j*k + kp - 1 (kp = min(k, L - j*k)); it reads T_{jk} and writes the
+    kp bitmaps and, unless it is the last pass, T_{jk+kp}."""
     NB = (n + 511) // 512
     bits = 16 * NB * 4
     directory = 8 * (NB + 1)
+    if kind in ("fused", "directory", "tile_count"):
+        l0 = level_index * k
+        kp = max(0, min(k, L - l0))
+        if kind == "directory":       # reads the pass's bitmaps, writes their directories
+            return kp * (bits + directory)
+        if kind == "tile_count":      # reads T_l once more for the per-tile digit counts
+            return n * b
+        return n * b + (0 if l0 + kp >= L else n * b) + kp * bits
     if kind == "prepass":             # reads S; tile counts and histogram are small
         return n * b
     if kind == "split":               # reads T_l, writes T_{l+1}, B_l and its directory
@@ -279,10 +290,12 @@ def main_ours(args):
     t_gen = time.perf_counter() - t_gen
     d_S = wt._torch_symbols(S)
     matrix = args.shape == "matrix"
-    tree = (wt.WaveletMatrix if matrix else wt.WaveletTree)(n, sigma, sb, tile_threads=args.tile_threads)
+    tree = (wt.WaveletMatrix if matrix else wt.WaveletTree)(n, sigma, sb, tile_threads=args.tile_threads,
+                                                            levels_per_pass=args.levels_per_pass)
     stream = torch.cuda.current_stream(dev)
     inf = tree.info()
     L = inf.levels
+    K = inf.levels_per_pass
     kernels = tree.kernels_per_build()
 
     for _ in range(max(args.warmup, 0)):
@@ -312,44 +325,56 @@ def main_ours(args):
     prof = tree.profile_read()
     tree.profile(False)
 
-    # per-kernel statistics over the timed region
+    # per-kernel statistics over the timed region; the dominant kernel is the
+    # split pass (one level per pass) or the k-level pass
+    fused = K > 1
+    main_kind = "fused" if fused else "split"
+    n_main = (L + K - 1) // K if fused else max(L - 1, 0)
     per_kind = {}
-    split_bytes = split_ms = 0.0
-    split_launches = 0
-    level = 0
-    per_level = [[0, 0.0] for _ in range(max(L - 1, 0))]
+    main_bytes = main_ms = 0.0
+    main_launches = 0
+    idx = 0
+    per_pass = [[0, 0.0] for _ in range(n_main)]
     for kind, ms in prof:
         if kind == "prepass":
-            level = 0
+            idx = 0
         per_kind.setdefault(kind, [0, 0.0])
         per_kind[kind][0] += 1
         per_kind[kind][1] += ms
-        if kind == "split":
-            split_bytes += algorithmic_bytes("split", level, n, sb, L)
-            split_ms += ms
-            split_launches += 1
-            if level < len(per_level):
-                per_level[level][0] += 1
-                per_level[level][1] += ms
-            level += 1
+        if kind == main_kind:
+            j = idx % max(n_main, 1)  # pass (or level) index within its build
+            main_bytes += algorithmic_bytes(kind, j, n, sb, L, K)
+            main_ms += ms
+            main_launches += 1
+            per_pass[j][0] += 1
+            per_pass[j][1] += ms
+            idx += 1
     total_kernel_ms = sum(v[1] for v in per_kind.values())
     peak, peak_kind = measured_hbm_peak()
-    achieved = split_bytes / (split_ms * 1e-3) / 1e9 if split_ms else 0.0
-    build_bytes = (algorithmic_bytes("prepass", 0, n, sb, L)
-                   + sum(algorithmic_bytes("split", l, n, sb, L) for l in range(L - 1))
-                   + algorithmic_bytes("leaf", L - 1, n, sb, L))
+    achieved = main_bytes / (main_ms * 1e-3) / 1e9 if main_ms else 0.0
+    build_bytes = algorithmic_bytes("prepass", 0, n, sb, L)
+    if fused:
+        build_bytes += sum(algorithmic_bytes("fused", j, n, sb, L, K) + algorithmic_bytes("directory", j, n, sb, L, K)
+                           + algorithmic_bytes("tile_count", j, n, sb, L, K) for j in range(n_main))
+        if matrix:
+            build_bytes -= algorithmic_bytes("prepass", 0, n, sb, L)  # the first count kernel checks the range
+    else:
+        build_bytes += (sum(algorithmic_bytes("split", l, n, sb, L) for l in range(L - 1))
+                        + algorithmic_bytes("leaf", L - 1, n, sb, L))
     if not matrix:
         build_bytes += algorithmic_bytes("hist_scan", 0, n, sb, L) + algorithmic_bytes("tables", 0, n, sb, L)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": (profiled_traffic() if args.config == 2 and n == CONFIGS[2]["n"] and not matrix
-                            else None),
-                "kernel": "k_split (per-level split pass)",
+                            and not fused else None),
+                "kernel": (f"k_fused ({K} levels per pass: reads T_l once, writes T_(l+{K}) and {K} bitmaps)"
+                           if fused else "k_split (per-level split pass)"),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy-based)",
-                "algorithmic_bytes_per_launch": split_bytes / max(split_launches, 1),
-                "mean_launch_ms": split_ms / max(split_launches, 1),
-                "time_share": round(split_ms / total_kernel_ms, 4) if total_kernel_ms else None,
-                "split_ms_per_level": [round(t / c, 4) if c else None for c, t in per_level],
+                "algorithmic_bytes_per_launch": main_bytes / max(main_launches, 1),
+                "mean_launch_ms": main_ms / max(main_launches, 1),
+                "time_share": round(main_ms / total_kernel_ms, 4) if total_kernel_ms else None,
+                ("fused_ms_per_pass" if fused else "split_ms_per_level"):
+                    [round(t / c, 4) if c else None for c, t in per_pass],
                 "whole_build_gbs": round(build_bytes / (ms_step * 1e-3) / 1e9, 1)}
 
     # end to end through the public host-buffer entry point
@@ -439,6 +464,7 @@ def main_ours(args):
                                            else "levelwise wavelet tree (Fig. 1)",
                                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                                            "tile_threads": args.tile_threads or "auto",
+                                           "levels_per_pass": K,
                                            "generate_s": round(t_gen, 2)}, cfg=args.config, n=n),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": kernels * args.steps,
@@ -798,7 +824,9 @@ def main(argv=None):
     ap.add_argument("--tile-threads", type=int, default=0)
     ap.add_argument("--shape", choices=["tree", "matrix"], default="tree",
                     help="levelwise wavelet tree (default) or wavelet matrix (Section 7)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--levels-per-pass", type=int, default=0,
+                    help="levels built per pass (1-4); 0 = the library's choice")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

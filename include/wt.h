@@ -88,6 +88,7 @@ typedef struct {
   uint64_t *d_rank;
   uint64_t *d_zeros;
   uint64_t *d_node_start;
+  uint32_t levels_per_pass; /* the schedule the builds use (see wt_config) */
 } wt_info_t;
 
 /*
@@ -101,12 +102,20 @@ typedef struct {
  *                  test hook: 1 + the tile index (of every pass) that never
  *                  publishes its look-back status, so that its successor's
  *                  bounded wait runs out.  0 = off.
+ *   levels_per_pass
+ *                  1: one split pass per level (Fig. 1's level loop).
+ *                  2..4: passes that each build that many levels (the
+ *                  multiary bucketing of Section 7 applied to the level
+ *                  passes): one pass reads T_l once, writes the bitmaps of
+ *                  levels l..l+k-1 and T_{l+k}, and a directory pass
+ *                  follows.  0 = the library's choice.  Above 4: WT_ERR_ARG.
  */
 typedef struct {
   uint32_t tile_threads;
   uint32_t ctas_per_sm;
   uint32_t spin_limit;
   uint32_t debug_skip_publish;
+  uint32_t levels_per_pass;
 } wt_config;
 
 /*
@@ -167,7 +176,11 @@ int wt_build_host(wt_tree *tree, const void *h_seq, uint32_t *h_bits, uint64_t *
  * l = 0..L-2 the split pass of the tree with a single node: zeros go to
  * j - R(j), ones to Z_l + R(j), where Z_l is the level's zero count, known
  * before the pass from the previous pass's tile counts.  The last level
- * writes bits and directory only.
+ * writes bits and directory only.  With levels_per_pass = k > 1 (the
+ * library's choice for 4-byte symbols and at least 8 levels) each pass
+ * builds k levels: a class of i bits goes to the start of its class in
+ * T_{l+i} (the classes ordered by their bits read from the last level to
+ * the first) plus the symbols of that class before it; no pre-pass runs.
  * Errors: as wt_create / wt_rebuild.
  */
 int wt_matrix_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,

@@ -1,9 +1,9 @@
 """Autotuner for the launch parameters of the level passes.
 
-Chooses the CTA size (tile = 32 * threads symbols) by timing each candidate
-on the device through the C ABI, and caches the winner in a JSON file keyed
-by the GPU name and a size class of the problem, so that later runs skip the
-search.  Cache file: $WT_AUTOTUNE_CACHE, else
+Chooses the CTA size (tile = 32 * threads symbols) and the number of levels
+built per pass by timing each candidate on the device through the C ABI, and
+caches the winner in a JSON file keyed by the GPU name and a size class of
+the problem, so that later runs skip the search.  Cache file: $WT_AUTOTUNE_CACHE, else
 ~/.cache/paper_1407_8142_gb300/autotune.json.
 """
 from __future__ import annotations
@@ -91,6 +91,30 @@ def tune_single(seq, sigma: int, candidates=(128, 256, 512), reps: int = 3, use_
                 raise RuntimeError("build failed during autotuning")
     best = min(times, key=times.get)
     _store(key, {"tile_threads": best, "ms": times})
+    return best
+
+
+def tune_levels_per_pass(seq, sigma: int, matrix: bool = False, candidates=(1, 2, 3, 4), reps: int = 3,
+                         use_cache: bool = True) -> int:
+    """Best levels per pass (1 = one split pass per level, k > 1 = passes that
+    build k levels each) for building `seq` as a tree or a wavelet matrix."""
+    from . import wt
+    t = wt._torch_symbols(seq)
+    n, b = t.numel(), t.element_size()
+    key = single_key(n, sigma, b) + ("|matrix" if matrix else "|tree") + "|levels_per_pass"
+    if use_cache:
+        hit = _load().get(key)
+        if hit:
+            return int(hit["levels_per_pass"])
+    cls = wt.WaveletMatrix if matrix else wt.WaveletTree
+    times = {}
+    for k in candidates:
+        with cls(n, sigma, b, levels_per_pass=k) as tree:
+            times[k] = _time(lambda: tree.build(t), reps)
+            if tree.sync() != 0:
+                raise RuntimeError("build failed during autotuning")
+    best = min(times, key=times.get)
+    _store(key, {"levels_per_pass": best, "ms": times})
     return best
 
 

@@ -32,6 +32,7 @@
 #include <new>
 
 #include "wt_dev.cuh"
+#include "wt_fused.h"
 #include "wt_internal.h"
 
 using namespace wtk;
@@ -324,8 +325,59 @@ int launch_node_tables(Launcher &ln, uint32_t m) {
   return WT_OK;
 }
 
+// k levels per pass.  The tree first runs the pre-pass (histogram, range
+// check), node starts, level tables and F tables; the matrix needs none of
+// them (its first count kernel checks the range).  Then per pass: the digit
+// counts of its tiles and their scan, the zeroing of its inner rows, the
+// k-level pass and the directories of its rows.
+template <int SB, int THREADS>
+int run_build_fused(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
+  Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
+  int rc;
+  const bool tree = t->shape == WT_SHAPE_TREE;
+  if (tree) {
+    if ((rc = launch_prepass<SB, THREADS>(ln, seq, seq_padded))) return rc;
+    if ((rc = launch_tables(ln))) return rc;
+    if (t->L >= 2) {
+      ln.before(kTables);
+      if ((rc = fused_tables(t, st, ln.lb(), ln.ticket()))) return rc;
+      ln.after();
+      ++ln.pass;
+    }
+  }
+  const uint8_t *in = seq;
+  bool padded = seq_padded;
+  for (uint32_t l = 0, j = 0; l < t->L; ++j) {
+    const uint32_t K = std::min(t->fuse_k, t->L - l);
+    const bool last = l + K == t->L;
+    ln.before(kTileCount);
+    if ((rc = fused_count(t, st, in, l, K, !tree && l == 0))) return rc;
+    ln.after();
+    ln.before(kTileScan);
+    if ((rc = fused_scan(t, st, K))) return rc;
+    ln.after();
+    if (K > 1) WT_CUDA(cudaMemsetAsync(t->d_bits + (uint64_t)(l + 1) * t->W, 0, (uint64_t)(K - 1) * t->W * 4, st));
+    uint8_t *out = last ? nullptr : static_cast<uint8_t *>(t->d_buf[j & 1]);
+    ln.before(kFused);
+    if ((rc = fused_pass(t, st, in, padded, out, l, K, ln.ticket()))) return rc;
+    ln.after();
+    ++ln.pass;
+    ln.before(kDirectory);
+    if ((rc = fused_dir(t, st, l, K, ln.lb(), ln.ticket()))) return rc;
+    ln.after();
+    ++ln.pass;
+    if (t->record_levels)
+      for (uint32_t m = l; m < l + K; ++m) WT_CUDA(cudaEventRecord(t->level_ev[m], st));
+    in = out;
+    padded = true;
+    l += K;
+  }
+  return WT_OK;
+}
+
 template <int SB, int THREADS>
 int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
+  if (t->fuse_k > 1) return run_build_fused<SB, THREADS>(t, seq, seq_padded, st);
   Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
   int rc;
   if ((rc = launch_prepass<SB, THREADS>(ln, seq, seq_padded))) return rc;
@@ -364,6 +416,8 @@ void release(wt_tree *t) {
   cudaFree(t->d_zeros);
   cudaFree(t->d_node_start);
   cudaFree(t->d_tab);
+  cudaFree(t->d_ftab);
+  cudaFree(t->d_fcount);
   cudaFree(t->d_ctrl);
   cudaFree(t->d_buf[0]);
   cudaFree(t->d_buf[1]);
@@ -393,6 +447,17 @@ uint32_t pick_threads(uint64_t n, uint32_t sb, int sms, uint32_t requested) {
   return 128;
 }
 
+// Levels per pass when the caller leaves the choice to the library, as
+// measured on GB300: four for the wavelet matrix of 4-byte symbols with at
+// least 8 levels (its one-level pass runs near the copy bandwidth, so
+// reading and writing the symbols once per four levels pays; config 3:
+// 7.13 ms against 7.89 ms); one everywhere else (at 1-byte symbols the
+// one-level pass is bound by instruction issue, not by memory, and the
+// tree's k-level passes need the full 2^L-bin histogram).
+uint32_t auto_levels_per_pass(uint32_t shape, uint32_t symbol_bytes, uint32_t L) {
+  return (shape == WT_SHAPE_MATRIX && symbol_bytes == 4 && L >= 8) ? 4u : 1u;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -414,6 +479,7 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   if (cfg && cfg->tile_threads && !(cfg->tile_threads == 128 || cfg->tile_threads == 256 ||
                                     cfg->tile_threads == 512))
     return WT_ERR_ARG;
+  if (cfg && cfg->levels_per_pass > kMaxLevelsPerPass) return WT_ERR_ARG;
 
   wt_tree *t = new (std::nothrow) wt_tree();
   if (!t) return WT_ERR_OOM;
@@ -435,13 +501,17 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   // symbols, and for long sequences, where the histogram's shared-memory
   // atomics cost the pre-pass more than one small table kernel per level
   // costs; short sequences of small alphabets keep it (fewer launches)
-  t->node_counts = shape == WT_SHAPE_TREE && L >= 2 &&
+  t->fuse_k = t->cfg.levels_per_pass ? t->cfg.levels_per_pass : auto_levels_per_pass(shape, symbol_bytes, L);
+  // the k-level passes of a tree take their tables from the histogram
+  t->node_counts = shape == WT_SHAPE_TREE && L >= 2 && t->fuse_k == 1 &&
                    ((1ull << L) > kHistSmemMaxBins || n >= (1ull << 24));
   t->NB = (n + 511) / 512;
   t->W = 16 * t->NB;
   t->threads = pick_threads(n, symbol_bytes, t->sms, t->cfg.tile_threads);
   t->T = 32ull * t->threads;
   t->NT = std::max<uint64_t>(1, (n + t->T - 1) / t->T);
+  t->tile_f = fused_tile_symbols(symbol_bytes);
+  t->NTf = std::max<uint64_t>(1, (n + t->tile_f - 1) / t->tile_f);
 
   auto fail = [&](cudaError_t e) {
     (void)cudaGetLastError();
@@ -452,6 +522,8 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   cudaError_t e;
   const bool tree = shape == WT_SHAPE_TREE;
   const uint64_t nbins = tree ? 1ull << L : 0;  // the matrix needs no histogram or node tables
+  // histogram words: the tree's 2^L bins, or the matrix's digit counts of its k-level passes
+  const uint64_t hist_words = tree ? nbins : (t->fuse_k > 1 ? 256 : 0);
   const size_t Lz = std::max<uint32_t>(L, 1);
   if ((e = cudaMalloc(&t->d_bits, std::max<size_t>(4, Lz * t->W * 4)))) return fail(e);
   if ((e = cudaMalloc(&t->d_rank, Lz * (t->NB + 1) * 8))) return fail(e);
@@ -459,18 +531,24 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   if (tree) {
     if ((e = cudaMalloc(&t->d_node_start, (nbins + 1) * 8))) return fail(e);
     if ((e = cudaMalloc(&t->d_tab, std::max<uint64_t>(1, nbins / 2) * sizeof(uint2)))) return fail(e);
+    if (t->fuse_k > 1 && L >= 2 && (e = cudaMalloc(&t->d_ftab, nbins * 4))) return fail(e);
   }
+  if (t->fuse_k > 1 && (e = cudaMalloc(&t->d_fcount, (2 * t->NTf << t->fuse_k) * 4))) return fail(e);
   t->counts_per_level = t->NT + (t->NT >> 6) + 1 + (t->NT >> 12) + 1;
-  t->ctrl_words = kCtrlWords + nbins + (uint64_t)Lz * t->counts_per_level;
+  t->ctrl_words = kCtrlWords + hist_words + (uint64_t)Lz * t->counts_per_level;
   if ((e = cudaMalloc(&t->d_ctrl, t->ctrl_words * 4))) return fail(e);
   t->d_hist = t->d_ctrl + kCtrlWords;
-  t->d_counts = t->d_hist + nbins;
-  t->buf_bytes = t->NT * t->T * symbol_bytes + 16;
+  t->d_counts = t->d_hist + hist_words;
+  // whole tiles of either schedule
+  t->buf_bytes = std::max(t->NT * t->T, t->NTf * t->tile_f) * symbol_bytes + 16;
   if (L >= 2) {
     if ((e = cudaMalloc(&t->d_buf[0], t->buf_bytes))) return fail(e);
     if ((e = cudaMalloc(&t->d_buf[1], t->buf_bytes))) return fail(e);
   }
   t->status_n = std::max<uint64_t>({t->NT, (uint64_t)hist_blocks(L), (uint64_t)tables_blocks(L), 1});
+  if (t->fuse_k > 1)
+    t->status_n = std::max<uint64_t>({t->status_n, (uint64_t)fused_tables_blocks(L, t->fuse_k),
+                                      (uint64_t)t->fuse_k * fused_dir_chunks(t->NB)});
   if ((e = cudaMalloc(&t->d_status, t->status_n * 8))) return fail(e);
   if ((e = cudaMemset(t->d_status, 0, t->status_n * 8))) return fail(e);
   if ((e = cudaMemset(t->d_zeros, 0, Lz * 8))) return fail(e);
@@ -507,7 +585,7 @@ int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
     // TMA and vector loads need 16-byte alignment: stage the input.
     void *dst = t->L >= 2 ? t->d_buf[1] : nullptr;
     if (!dst) {
-      if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->NT * t->T * t->sb + 16));
+      if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->buf_bytes));
       dst = t->d_in_host;
     }
     WT_CUDA(cudaMemcpyAsync(dst, seq, t->n * t->sb, cudaMemcpyDeviceToDevice, st));
@@ -571,7 +649,7 @@ int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_r
                   void *stream) {
   if (!t || (!h_seq && t->n) || t->owner) return WT_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->NT * t->T * t->sb + 16));
+  if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->buf_bytes));
   const uint32_t L = t->L;
   const bool copy_out = t->n && L && (h_bits || h_rank);
   if (copy_out && !t->copy_stream) {
@@ -613,6 +691,7 @@ int wt_info(const wt_tree *t, wt_info_t *info) {
   info->d_rank = reinterpret_cast<uint64_t *>(t->d_rank);
   info->d_zeros = reinterpret_cast<uint64_t *>(t->d_zeros);
   info->d_node_start = reinterpret_cast<uint64_t *>(t->d_node_start);
+  info->levels_per_pass = t->fuse_k;
   return WT_OK;
 }
 
@@ -648,6 +727,12 @@ int wt_profile_read(wt_tree *t, float *ms, int32_t *kind, int32_t cap) {
 int wt_kernels_per_build(const wt_tree *t) {
   if (!t) return WT_ERR_ARG;
   if (t->n == 0) return 0;
+  if (t->fuse_k > 1) {
+    int k = 0;
+    if (t->shape == WT_SHAPE_TREE) k += 2 + (t->L >= 2 ? 2 : 0);  // pre-pass, histogram scan, tables, F tables
+    k += 4 * (int)((t->L + t->fuse_k - 1) / t->fuse_k);   // per pass: counts, scan, k-level pass, directories
+    return k;
+  }
   int k = 1;                                              // pre-pass
   if (t->node_counts) k += (int)t->L - 1;                 // node tables, levels 1..L-1
   else if (t->shape == WT_SHAPE_TREE) k += 1 + (tables_blocks(t->L) ? 1 : 0);  // histogram scan, tables

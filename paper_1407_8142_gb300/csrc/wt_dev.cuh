@@ -56,27 +56,22 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
   return v;
 }
 
-// Called by one whole warp.  `tile` is this block's index in the status
-// array, `first` the index of the first tile of its segment (that tile's
-// exclusive prefix is 0).  Publishes the aggregate, walks back over the
-// predecessors 32 at a time, publishes the inclusive prefix and returns the
-// exclusive prefix (same value in every lane).  Every wait is bounded: after
+// Called by one whole warp after the tile's aggregate is published: walks
+// back over the predecessors of `tile` in its segment (which starts at tile
+// `first`), 32 at a time, and returns the tile's exclusive prefix (same value
+// in every lane).  A window is used as soon as, counting from the nearest
+// predecessor, every entry up to the first inclusive prefix is published
+// (entries behind that prefix are not waited for); a window of aggregates
+// only is summed and the walk moves on.  Every wait is bounded: after
 // spin_limit polls the missing predecessors count as zero, WT_ERR_TIMEOUT is
 // latched, and the pass runs to completion.
-static __device__ __noinline__ uint32_t lookback(const Lookback &lb, uint32_t tile, uint32_t first,
-                                          uint32_t aggregate) {
+__device__ __forceinline__ uint32_t lookback_walk(const Lookback &lb, uint32_t tile, uint32_t first) {
   const uint32_t lane = threadIdx.x & 31;
-  const bool publish = (lb.skip == 0) || (tile != lb.skip - 1);
-  if (tile == first) {
-    if (lane == 0 && publish) st_relaxed(&lb.status[tile], pack_status(kFlagP, lb.epoch, aggregate));
-    return 0;
-  }
-  if (lane == 0 && publish) st_relaxed(&lb.status[tile], pack_status(kFlagA, lb.epoch, aggregate));
   uint32_t exclusive = 0;
   long long pred = (long long)tile - 1;
   uint32_t spins = 0;
   bool timed_out = false;
-  for (;;) {
+  while (pred >= (long long)first) {
     const long long idx = pred - (long long)lane;
     uint32_t flag, val;
     for (;;) {
@@ -89,7 +84,10 @@ static __device__ __noinline__ uint32_t lookback(const Lookback &lb, uint32_t ti
         flag = kFlagP;  // before the segment: contributes nothing, stops the walk
         val = 0;
       }
-      if (__all_sync(0xFFFFFFFFu, flag != kFlagX)) break;
+      const uint32_t xm = __ballot_sync(0xFFFFFFFFu, flag == kFlagX);
+      const uint32_t pm = __ballot_sync(0xFFFFFFFFu, flag == kFlagP);
+      const uint32_t pk = pm & (0u - pm);  // nearest inclusive prefix
+      if (pk ? (xm & (pk - 1u)) == 0u : xm == 0u) break;
       ++spins;
       // give up after spin_limit polls, or at once when another wait of this
       // build already gave up (bounds the total delay of a failed build)
@@ -115,9 +113,37 @@ static __device__ __noinline__ uint32_t lookback(const Lookback &lb, uint32_t ti
     pred -= 32;
   }
   if (timed_out && lane == 0) latch_error(lb.err, WT_ERR_TIMEOUT);
-  if (lane == 0 && publish)
-    st_relaxed(&lb.status[tile], pack_status(kFlagP, lb.epoch, exclusive + aggregate));
   return exclusive;
+}
+
+// Publish `v` with `flag` for `tile` (one thread), unless the test hook
+// withholds this tile.
+__device__ __forceinline__ void lookback_publish(const Lookback &lb, uint32_t tile, uint32_t flag,
+                                                 uint32_t v) {
+  if ((lb.skip == 0) || (tile != lb.skip - 1)) st_relaxed(&lb.status[tile], pack_status(flag, lb.epoch, v));
+}
+
+// Called by one whole warp.  `tile` is this block's index in the status
+// array, `first` the index of the first tile of its segment (that tile's
+// exclusive prefix is 0).  Publishes the aggregate, walks back, publishes
+// the inclusive prefix and returns the exclusive prefix.
+__device__ __forceinline__ uint32_t lookback_inline(const Lookback &lb, uint32_t tile, uint32_t first,
+                                                   uint32_t aggregate) {
+  const uint32_t lane = threadIdx.x & 31;
+  if (tile == first) {
+    if (lane == 0) lookback_publish(lb, tile, kFlagP, aggregate);
+    return 0;
+  }
+  if (lane == 0) lookback_publish(lb, tile, kFlagA, aggregate);
+  const uint32_t exclusive = lookback_walk(lb, tile, first);
+  if (lane == 0) lookback_publish(lb, tile, kFlagP, exclusive + aggregate);
+  return exclusive;
+}
+
+// Out-of-line copy for kernels that call it once per tile.
+static __device__ __noinline__ uint32_t lookback(const Lookback &lb, uint32_t tile, uint32_t first,
+                                                 uint32_t aggregate) {
+  return lookback_inline(lb, tile, first, aggregate);
 }
 
 // Block-wide exclusive scan of one uint32 per thread.  s_warp holds >= 33

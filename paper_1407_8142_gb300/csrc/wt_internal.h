@@ -13,7 +13,10 @@ constexpr uint32_t kCtrlWords = 128;    // [0,64) tickets, [64] error, rest rese
 constexpr uint32_t kCtrlErr = 64;
 constexpr uint32_t kMaxProfiled = 2048;  // kernel launches recorded per profiling window
 
-enum KernelKind : int32_t { kPrepass = 0, kHistScan = 1, kTables = 2, kSplit = 3, kLeaf = 4 };
+enum KernelKind : int32_t {
+  kPrepass = 0, kHistScan = 1, kTables = 2, kSplit = 3, kLeaf = 4, kFused = 5, kDirectory = 6,
+  kTileCount = 7, kTileScan = 8
+};
 
 }  // namespace wtk
 
@@ -24,6 +27,10 @@ struct wt_tree {
   // tree with a large alphabet: node sizes come from per-node counts kept by
   // the split passes instead of a 2^L-bin histogram of the input
   bool node_counts = false;
+  // levels per pass: 1 = one split pass per level; k > 1 = passes that each
+  // build k levels (their F tables in d_ftab, tiles of tile_f symbols)
+  uint32_t fuse_k = 1;
+  uint64_t tile_f = 0, NTf = 0;
   uint64_t W = 0, NB = 0;
   uint32_t threads = 0;         // CTA size of the level passes
   uint64_t T = 0;               // symbols per tile
@@ -38,6 +45,8 @@ struct wt_tree {
   unsigned long long *d_node_start = nullptr;
   // scratch
   uint2 *d_tab = nullptr;       // per level l (heap offset 2^l - 1): {O_l[p], E_{l+1}[2p+1]-O_l[p]}
+  uint32_t *d_ftab = nullptr;   // k-level passes of a tree: F_m at offset 2^m - 2, m = 1..L-1
+  uint32_t *d_fcount = nullptr; // k-level passes: per-tile digit counts, then their prefixes
   uint32_t *d_ctrl = nullptr;   // kCtrlWords control words, then 2^L words: the histogram
                                 // (tree) or the per-node ones counters (node_counts)
   uint32_t *d_hist = nullptr;

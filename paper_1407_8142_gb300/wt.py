@@ -26,7 +26,8 @@ WT_ERR_TIMEOUT = -5
 ERROR_NAMES = {WT_ERR_ARG: "WT_ERR_ARG", WT_ERR_OOM: "WT_ERR_OOM", WT_ERR_CUDA: "WT_ERR_CUDA",
                WT_ERR_SYMBOL: "WT_ERR_SYMBOL", WT_ERR_TIMEOUT: "WT_ERR_TIMEOUT"}
 
-KERNEL_KINDS = {0: "prepass", 1: "hist_scan", 2: "tables", 3: "split", 4: "leaf"}
+KERNEL_KINDS = {0: "prepass", 1: "hist_scan", 2: "tables", 3: "split", 4: "leaf", 5: "fused",
+                6: "directory", 7: "tile_count", 8: "tile_scan"}
 WT_SHAPE_TREE = 0
 WT_SHAPE_MATRIX = 1
 
@@ -39,7 +40,8 @@ class WTError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("tile_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("spin_limit", ctypes.c_uint32), ("debug_skip_publish", ctypes.c_uint32)]
+                ("spin_limit", ctypes.c_uint32), ("debug_skip_publish", ctypes.c_uint32),
+                ("levels_per_pass", ctypes.c_uint32)]
 
 
 class Info(ctypes.Structure):
@@ -48,7 +50,7 @@ class Info(ctypes.Structure):
                 ("shape", ctypes.c_uint32), ("words_per_level", ctypes.c_uint64),
                 ("blocks", ctypes.c_uint64), ("d_bits", ctypes.c_void_p),
                 ("d_rank", ctypes.c_void_p), ("d_zeros", ctypes.c_void_p),
-                ("d_node_start", ctypes.c_void_p)]
+                ("d_node_start", ctypes.c_void_p), ("levels_per_pass", ctypes.c_uint32)]
 
 
 _lib = None
@@ -262,8 +264,9 @@ class WaveletTree:
     _create = staticmethod(wt_create)
 
     def __init__(self, n: int, sigma: int, symbol_bytes: int, tile_threads: int = 0,
-                 ctas_per_sm: int = 0, spin_limit: int = 0, debug_skip_publish: int = 0):
-        self.cfg = Config(tile_threads, ctas_per_sm, spin_limit, debug_skip_publish)
+                 ctas_per_sm: int = 0, spin_limit: int = 0, debug_skip_publish: int = 0,
+                 levels_per_pass: int = 0):
+        self.cfg = Config(tile_threads, ctas_per_sm, spin_limit, debug_skip_publish, levels_per_pass)
         self.n, self.sigma, self.symbol_bytes = n, sigma, symbol_bytes
         self.handle = type(self)._create(n, sigma, symbol_bytes, self.cfg)
         self._keep = None
