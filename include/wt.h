@@ -137,7 +137,12 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
  * pass for level L-1 (bits and directory).  For sigma > 2^13 the pre-pass
  * builds no histogram: each split pass counts, per child node, the ones of
  * the next level, and a small kernel before each level turns these counts
- * into that level's node tables and node starts.  Every size is known on the host, so the call has no host
+ * into that level's node tables and node starts.  With levels_per_pass =
+ * k > 1 (see wt_config; the library's choice for 4-byte symbols, at least 8
+ * levels and n >= 2^22) each pass builds k levels, after a kernel that
+ * counts every tile's k-bit digits (and the node sizes of level l+k, which
+ * give that pass's tables) and a scan of those counts; a directory kernel
+ * follows each pass.  Every size is known on the host, so the call has no host
  * synchronisation and may be captured into a CUDA graph.
  * d_seq is read-only; it must stay valid until the stream work completes.
  * A d_seq that is not 16-byte aligned is first copied into tree scratch.

@@ -253,22 +253,27 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   return WT_OK;
 }
 
-int launch_tables(Launcher &ln) {
+// Node starts E[v] = symbols whose top log2(nbins) bits are < v.
+int launch_hist_scan(Launcher &ln, uint32_t nbins) {
   wt_tree *t = ln.t;
-  {
-    ScanArgs a;
-    a.hist = t->d_hist;
-    a.E = t->d_node_start;
-    a.nbins = 1u << t->L;
-    a.nblocks = hist_blocks(t->L);
-    a.ticket = ln.ticket();
-    a.lb = ln.lb();
-    ln.before(kHistScan);
-    k_hist_scan<<<a.nblocks, kScanThreads, 0, ln.st>>>(a);
-    ln.after();
-    ++ln.pass;
-    WT_CUDA(cudaGetLastError());
-  }
+  ScanArgs a;
+  a.hist = t->d_hist;
+  a.E = t->d_node_start;
+  a.nbins = nbins;
+  a.nblocks = (nbins + kScanChunk - 1) / kScanChunk;
+  a.ticket = ln.ticket();
+  a.lb = ln.lb();
+  ln.before(kHistScan);
+  k_hist_scan<<<a.nblocks, kScanThreads, 0, ln.st>>>(a);
+  ln.after();
+  ++ln.pass;
+  WT_CUDA(cudaGetLastError());
+  return WT_OK;
+}
+
+// Level tables of every level from the node starts of level L.
+int launch_level_tables(Launcher &ln) {
+  wt_tree *t = ln.t;
   const uint32_t nb = tables_blocks(t->L);
   if (nb) {
     TabArgs a;
@@ -285,6 +290,11 @@ int launch_tables(Launcher &ln) {
   }
   ++ln.pass;
   return WT_OK;
+}
+
+int launch_tables(Launcher &ln) {
+  if (int rc = launch_hist_scan(ln, 1u << ln.t->L)) return rc;
+  return launch_level_tables(ln);
 }
 
 // Tables of level m (1 <= m <= L-2) from the node counts of the previous
@@ -325,37 +335,41 @@ int launch_node_tables(Launcher &ln, uint32_t m) {
   return WT_OK;
 }
 
-// k levels per pass.  The tree first runs the pre-pass (histogram, range
-// check), node starts, level tables and F tables; the matrix needs none of
-// them (its first count kernel checks the range).  Then per pass: the digit
-// counts of its tiles and their scan, the zeroing of its inner rows, the
-// k-level pass and the directories of its rows.
+// k levels per pass (L >= 1).  No pre-pass: the first pass's count kernel
+// checks the symbol range.  Per pass over T_l with K levels: the digit
+// counts of its tiles and their scan; for the tree also the node counts of
+// level l+K (gathered by the count kernel), their scan into node starts and
+// the F tables of levels l+1..l+K; the zeroing of its inner rows, the
+// k-level pass and the directories of its rows.  The tree's level tables
+// (used by the queries) come last, from the node starts of level L.
 template <int SB, int THREADS>
 int run_build_fused(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
   Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
   int rc;
   const bool tree = t->shape == WT_SHAPE_TREE;
-  if (tree) {
-    if ((rc = launch_prepass<SB, THREADS>(ln, seq, seq_padded))) return rc;
-    if ((rc = launch_tables(ln))) return rc;
-    if (t->L >= 2) {
-      ln.before(kTables);
-      if ((rc = fused_tables(t, st, ln.lb(), ln.ticket()))) return rc;
-      ln.after();
-      ++ln.pass;
-    }
-  }
   const uint8_t *in = seq;
   bool padded = seq_padded;
   for (uint32_t l = 0, j = 0; l < t->L; ++j) {
     const uint32_t K = std::min(t->fuse_k, t->L - l);
-    const bool last = l + K == t->L;
+    const uint32_t top = l + K;
+    const bool last = top == t->L;
+    if (tree) WT_CUDA(cudaMemsetAsync(t->d_hist, 0, (4ull << top), st));
     ln.before(kTileCount);
-    if ((rc = fused_count(t, st, in, l, K, !tree && l == 0))) return rc;
+    if ((rc = fused_count(t, st, in, l, K, l == 0))) return rc;
     ln.after();
     ln.before(kTileScan);
     if ((rc = fused_scan(t, st, K))) return rc;
     ln.after();
+    if (tree) {
+      if ((rc = launch_hist_scan(ln, 1u << top))) return rc;
+      const uint32_t m_hi = std::min(top, t->L - 1);
+      if (m_hi >= l + 1) {
+        ln.before(kTables);
+        if ((rc = fused_tables(t, st, l + 1, m_hi, top, ln.lb(), ln.ticket()))) return rc;
+        ln.after();
+        ++ln.pass;
+      }
+    }
     if (K > 1) WT_CUDA(cudaMemsetAsync(t->d_bits + (uint64_t)(l + 1) * t->W, 0, (uint64_t)(K - 1) * t->W * 4, st));
     uint8_t *out = last ? nullptr : static_cast<uint8_t *>(t->d_buf[j & 1]);
     ln.before(kFused);
@@ -372,12 +386,13 @@ int run_build_fused(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_
     padded = true;
     l += K;
   }
+  if (tree && (rc = launch_level_tables(ln))) return rc;
   return WT_OK;
 }
 
 template <int SB, int THREADS>
 int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) {
-  if (t->fuse_k > 1) return run_build_fused<SB, THREADS>(t, seq, seq_padded, st);
+  if (t->fuse_k > 1 && t->L >= 1) return run_build_fused<SB, THREADS>(t, seq, seq_padded, st);
   Launcher ln{t, st, (t->build_count * kPasses) & kEpochMask};
   int rc;
   if ((rc = launch_prepass<SB, THREADS>(ln, seq, seq_padded))) return rc;
@@ -448,14 +463,16 @@ uint32_t pick_threads(uint64_t n, uint32_t sb, int sms, uint32_t requested) {
 }
 
 // Levels per pass when the caller leaves the choice to the library, as
-// measured on GB300: four for the wavelet matrix of 4-byte symbols with at
-// least 8 levels (its one-level pass runs near the copy bandwidth, so
+// measured on GB300: four for 4-byte symbols, at least 8 levels and
+// n >= 2^22 (the one-level pass runs near the copy bandwidth there, so
 // reading and writing the symbols once per four levels pays; config 3:
-// 7.13 ms against 7.89 ms); one everywhere else (at 1-byte symbols the
-// one-level pass is bound by instruction issue, not by memory, and the
-// tree's k-level passes need the full 2^L-bin histogram).
-uint32_t auto_levels_per_pass(uint32_t shape, uint32_t symbol_bytes, uint32_t L) {
-  return (shape == WT_SHAPE_MATRIX && symbol_bytes == 4 && L >= 8) ? 4u : 1u;
+// tree 9.46 ms against 9.91 ms, wavelet matrix 7.37 ms against 7.90 ms);
+// one everywhere else (at 1-byte symbols the one-level pass is bound by
+// instruction issue, not by memory; short sequences are bound by launch
+// latency, and a k-level pass takes six launches).
+uint32_t auto_levels_per_pass(uint32_t shape, uint32_t symbol_bytes, uint32_t L, uint64_t n) {
+  (void)shape;
+  return (symbol_bytes == 4 && L >= 8 && n >= (1ull << 22)) ? 4u : 1u;
 }
 
 }  // namespace
@@ -501,7 +518,7 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   // symbols, and for long sequences, where the histogram's shared-memory
   // atomics cost the pre-pass more than one small table kernel per level
   // costs; short sequences of small alphabets keep it (fewer launches)
-  t->fuse_k = t->cfg.levels_per_pass ? t->cfg.levels_per_pass : auto_levels_per_pass(shape, symbol_bytes, L);
+  t->fuse_k = t->cfg.levels_per_pass ? t->cfg.levels_per_pass : auto_levels_per_pass(shape, symbol_bytes, L, n);
   // the k-level passes of a tree take their tables from the histogram
   t->node_counts = shape == WT_SHAPE_TREE && L >= 2 && t->fuse_k == 1 &&
                    ((1ull << L) > kHistSmemMaxBins || n >= (1ull << 24));
@@ -727,10 +744,13 @@ int wt_profile_read(wt_tree *t, float *ms, int32_t *kind, int32_t cap) {
 int wt_kernels_per_build(const wt_tree *t) {
   if (!t) return WT_ERR_ARG;
   if (t->n == 0) return 0;
-  if (t->fuse_k > 1) {
+  if (t->fuse_k > 1 && t->L >= 1) {
     int k = 0;
-    if (t->shape == WT_SHAPE_TREE) k += 2 + (t->L >= 2 ? 2 : 0);  // pre-pass, histogram scan, tables, F tables
-    k += 4 * (int)((t->L + t->fuse_k - 1) / t->fuse_k);   // per pass: counts, scan, k-level pass, directories
+    for (uint32_t l = 0; l < t->L; l += t->fuse_k) {
+      k += 4;  // counts, their scan, the k-level pass, directories
+      if (t->shape == WT_SHAPE_TREE) k += 1 + (std::min(l + t->fuse_k, t->L - 1) >= l + 1 ? 1 : 0);  // node starts, F tables
+    }
+    if (t->shape == WT_SHAPE_TREE && t->L >= 2) k += 1;  // level tables
     return k;
   }
   int k = 1;                                              // pre-pass

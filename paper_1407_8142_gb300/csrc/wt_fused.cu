@@ -402,18 +402,37 @@ struct CountArgs {
   uint32_t n, L, level, NT;
   uint32_t sigma;      // range check of the input symbols (first pass), 0 = none
   uint32_t *tcnt;      // digit d of tile t at tcnt[d * NT + t]
+  uint32_t *ncount;    // tree: symbols per node of level level+K (zeroed), else null
   int *err;
 };
 
+constexpr uint32_t kSpanKeyed = 32;  // tiles over fewer nodes count them in shared memory
+
+// Count one symbol of a tile that spans nodes into its node of level l+K:
+// in shared memory (key = node offset from the tile's first node, digit)
+// when the tile spans fewer than kSpanKeyed nodes, else straight to global
+// memory (such tiles hold many small nodes, so there is no hot counter).
+template <uint32_t K>
+__device__ __forceinline__ void count_node(const CountArgs &a, uint32_t *sNC, uint32_t v, uint32_t p0,
+                                           bool keyed) {
+  const uint32_t q = v >> (a.L - a.level - K);
+  if (keyed) atomicAdd(&sNC[q - (p0 << K)], 1u);
+  else atomicAdd(&a.ncount[q], 1u);
+}
+
 // Symbols of each digit in each tile of T_l (tiles of the k-level pass).
 // One CTA per tile; per-thread counters in shared memory (thread t owns
-// column t, so there are no bank conflicts and no atomics).
+// column t, so there are no bank conflicts and no atomics).  For the tree
+// the kernel also counts the symbols of every node of level l+K, which the
+// pass's tables need: a tile within one node adds its digit counts to that
+// node's 2^K children.
 template <int SB, int K>
 __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
   using G = FGeom<SB>;
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t TS = G::TS, D = 1u << K;
   __shared__ uint32_t sH[D * kFThreads];
+  __shared__ uint32_t sNC[kSpanKeyed * D];
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t tile = blockIdx.x;
   const uint64_t start = (uint64_t)tile * TS;
@@ -422,6 +441,17 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
 #pragma unroll
   for (uint32_t d = 0; d < D; ++d) sH[d * kFThreads + tid] = 0;
   const uint8_t *base = a.in + start * SB;
+  const Sym *syms = reinterpret_cast<const Sym *>(base);
+  // the tile's nodes of level l (T_l is ordered by node)
+  const uint32_t ps = a.L - a.level;
+  const bool tree_node = a.ncount != nullptr && a.level != 0;
+  const uint32_t p0 = tree_node ? (((uint32_t)syms[0] & lmask) >> ps) : 0u;
+  const uint32_t p1 = tree_node ? (((uint32_t)syms[nv - 1] & lmask) >> ps) : 0u;
+  const bool nodes = a.ncount != nullptr && p0 != p1;  // count nodes per symbol
+  const bool keyed = p1 - p0 < kSpanKeyed;
+  if (nodes && keyed)
+    for (uint32_t i = tid; i < kSpanKeyed * D; i += kFThreads) sNC[i] = 0;
+  if (nodes) __syncthreads();
   const uint32_t full = (nv * SB) >> 4;  // whole 16-byte chunks
   uint32_t mx = 0;
   for (uint32_t q = tid; q < full; q += kFThreads) {
@@ -434,13 +464,15 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
         const uint32_t raw = SB == 4 ? words[c] : (words[c] >> (8 * SB * e)) & ((1u << (8 * SB)) - 1u);
         mx = max(mx, raw);
         sH[(((raw & lmask) >> dsh) & (D - 1)) * kFThreads + tid] += 1u;
+        if (nodes) count_node<K>(a, sNC, raw & lmask, p0, keyed);
       }
     }
   }
   for (uint32_t x = full * (16 / SB) + tid; x < nv; x += kFThreads) {
-    const uint32_t raw = reinterpret_cast<const Sym *>(base)[x];
+    const uint32_t raw = syms[x];
     mx = max(mx, raw);
     sH[(((raw & lmask) >> dsh) & (D - 1)) * kFThreads + tid] += 1u;
+    if (nodes) count_node<K>(a, sNC, raw & lmask, p0, keyed);
   }
   if (a.sigma && mx >= a.sigma) latch_error(a.err, WT_ERR_SYMBOL);
   __syncthreads();
@@ -448,7 +480,14 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
     uint32_t s = 0;
     for (uint32_t k = lane; k < kFThreads; k += 32) s += sH[d * kFThreads + k];
     s = __reduce_add_sync(0xFFFFFFFFu, s);
-    if (lane == 0) a.tcnt[(uint64_t)d * a.NT + tile] = s;
+    if (lane == 0) {
+      a.tcnt[(uint64_t)d * a.NT + tile] = s;
+      if (a.ncount && !nodes && s) atomicAdd(&a.ncount[(p0 << K) | d], s);  // one node
+    }
+  }
+  if (nodes && keyed) {
+    for (uint32_t i = tid; i < kSpanKeyed * D && (i >> K) <= p1 - p0; i += kFThreads)
+      if (sNC[i]) atomicAdd(&a.ncount[(p0 << K) + i], sNC[i]);
   }
 }
 
@@ -549,16 +588,17 @@ __global__ void __launch_bounds__(kScanThreads) k_dir(DirArgs a) {
 
 // ------------------------------------------------------------------ F tables
 struct FTabArgs {
-  const unsigned long long *E;  // node starts: E[v] = symbols < v, 2^L + 1 entries
+  const unsigned long long *E;  // E[v] = symbols whose top Ltop bits are < v, 2^Ltop + 1 entries
   uint32_t *F;                  // F_m at F + 2^m - 2
-  uint32_t L, K, nblocks;
+  uint32_t L, K, Ltop, m_lo, m_hi, nblocks;
   uint32_t *ticket;
   Lookback lb;
 };
 
-// Level m (1 <= m <= L-1) is built by the pass starting at l = K floor((m-1)/K),
-// as granularity i = m - l.  For node q = p 2^i + c of level m:
-//   F_m[q] = E[q << (L-m)] - sum over p' < p of |node p' 2^i + c|.
+// Level m (m_lo <= m <= m_hi, m_hi <= Ltop) is built by the pass starting at
+// l = K floor((m-1)/K), as granularity i = m - l.  For node q = p 2^i + c
+// of level m:
+//   F_m[q] = E[q << (Ltop-m)] - sum over p' < p of |node p' 2^i + c|.
 // Blocks walk levels, then classes c, then chunks of p; every (m, c) is one
 // look-back segment.
 __global__ void __launch_bounds__(kScanThreads) k_fuse_tables(FTabArgs a) {
@@ -569,8 +609,8 @@ __global__ void __launch_bounds__(kScanThreads) k_fuse_tables(FTabArgs a) {
   __syncthreads();
   const uint32_t tile = s_tile;
   if (tile >= a.nblocks) return;
-  uint32_t first = 0, m = 1, l = 0, i = 1, nch = 1;
-  for (; m < a.L; ++m) {
+  uint32_t first = 0, m = a.m_lo, l = 0, i = 1, nch = 1;
+  for (; m <= a.m_hi; ++m) {
     l = a.K * ((m - 1) / a.K);
     i = m - l;
     nch = ((1u << l) + kScanChunk - 1) / kScanChunk;
@@ -579,7 +619,7 @@ __global__ void __launch_bounds__(kScanThreads) k_fuse_tables(FTabArgs a) {
   }
   const uint32_t c = (tile - first) / nch, chunk = (tile - first) - c * nch;
   const uint32_t seg_first = first + c * nch;
-  const uint32_t sh = a.L - m, cntp = 1u << l;
+  const uint32_t sh = a.Ltop - m, cntp = 1u << l;
   const uint32_t p0 = chunk * kScanChunk + tid * kScanItems;
   uint32_t sz[kScanItems];
   uint32_t sum = 0;
@@ -669,9 +709,11 @@ uint32_t fused_tile_symbols(uint32_t symbol_bytes) {
   return symbol_bytes == 4 ? FGeom<4>::TS : symbol_bytes == 2 ? FGeom<2>::TS : FGeom<1>::TS;
 }
 
-uint32_t fused_tables_blocks(uint32_t L, uint32_t K) {
+uint32_t fused_tables_blocks(uint32_t L, uint32_t K) { return fused_tables_blocks_range(1, L - 1, K); }
+
+uint32_t fused_tables_blocks_range(uint32_t m_lo, uint32_t m_hi, uint32_t K) {
   uint32_t nb = 0;
-  for (uint32_t m = 1; m < L; ++m) {
+  for (uint32_t m = m_lo; m <= m_hi && m >= 1; ++m) {
     const uint32_t l = K * ((m - 1) / K), i = m - l;
     nb += (((1u << l) + kScanChunk - 1) / kScanChunk) << i;
   }
@@ -689,6 +731,7 @@ int fused_count(wt_tree *t, cudaStream_t st, const uint8_t *in, uint32_t level, 
   a.NT = (uint32_t)t->NTf;
   a.sigma = check ? t->sigma : 0u;
   a.tcnt = t->d_fcount;
+  a.ncount = t->shape == WT_SHAPE_TREE ? t->d_hist : nullptr;
   a.err = reinterpret_cast<int *>(t->d_ctrl + kCtrlErr);
   switch (t->sb) {
     case 1: return launch_count_sb<1>(st, a, K);
@@ -737,13 +780,17 @@ int fused_pass(wt_tree *t, cudaStream_t st, const uint8_t *in, bool in_padded, u
   return WT_ERR_ARG;
 }
 
-int fused_tables(wt_tree *t, cudaStream_t st, const Lookback &lb, uint32_t *ticket) {
+int fused_tables(wt_tree *t, cudaStream_t st, uint32_t m_lo, uint32_t m_hi, uint32_t Ltop, const Lookback &lb,
+                 uint32_t *ticket) {
   FTabArgs a;
   a.E = t->d_node_start;
   a.F = t->d_ftab;
   a.L = t->L;
   a.K = t->fuse_k;
-  a.nblocks = fused_tables_blocks(t->L, t->fuse_k);
+  a.Ltop = Ltop;
+  a.m_lo = m_lo;
+  a.m_hi = m_hi;
+  a.nblocks = m_hi >= m_lo ? fused_tables_blocks_range(m_lo, m_hi, t->fuse_k) : 0;
   a.ticket = ticket;
   a.lb = lb;
   if (!a.nblocks) return WT_OK;

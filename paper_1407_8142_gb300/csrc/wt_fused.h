@@ -19,8 +19,9 @@ uint32_t fused_tables_blocks(uint32_t L, uint32_t K);
 uint32_t fused_dir_chunks(uint64_t NB);
 
 // Digit counts of every tile of T_level (K levels: 2^K digits), checking
-// the symbols against sigma when `check` is set; then their exclusive scan
-// over the tiles (and, for the matrix, the digit totals).
+// the symbols against sigma when `check` is set, and for the tree the node
+// counts of level level+K into d_hist (zeroed by the caller); then their
+// exclusive scan over the tiles (and, for the matrix, the digit totals).
 int fused_count(wt_tree *t, cudaStream_t st, const uint8_t *in, uint32_t level, uint32_t K, bool check);
 int fused_scan(wt_tree *t, cudaStream_t st, uint32_t K);
 
@@ -30,8 +31,11 @@ int fused_scan(wt_tree *t, cudaStream_t st, uint32_t K);
 int fused_pass(wt_tree *t, cudaStream_t st, const uint8_t *in, bool in_padded, uint8_t *out,
                uint32_t level, uint32_t K, uint32_t *ticket);
 
-// F tables of every level 1..L-1 from the node starts E (tree only).
-int fused_tables(wt_tree *t, cudaStream_t st, const Lookback &lb, uint32_t *ticket);
+// F tables of levels m_lo..m_hi (tree only) from E = d_node_start, the
+// exclusive scan of the node counts of level Ltop (m_hi <= Ltop).
+int fused_tables(wt_tree *t, cudaStream_t st, uint32_t m_lo, uint32_t m_hi, uint32_t Ltop, const Lookback &lb,
+                 uint32_t *ticket);
+uint32_t fused_tables_blocks_range(uint32_t m_lo, uint32_t m_hi, uint32_t K);
 
 // Directories and zero counts of rows level0..level0+levels-1.
 int fused_dir(wt_tree *t, cudaStream_t st, uint32_t level0, uint32_t levels, const Lookback &lb,

@@ -189,19 +189,23 @@ def test_bad_levels_per_pass(wt):
 
 
 def test_library_choice(wt):
-    # k = 4 for the wavelet matrix of 4-byte symbols with >= 8 levels, else 1
-    with wt.WaveletMatrix(1000, 1 << 20, 4) as m:
-        assert m.info().levels_per_pass == 4
-    with wt.WaveletMatrix(1000, 100, 4) as m:
-        assert m.info().levels_per_pass == 1
-    with wt.WaveletMatrix(1000, 256, 1) as m:
-        assert m.info().levels_per_pass == 1
-    with wt.WaveletTree(1000, 1 << 20, 4) as t:
-        assert t.info().levels_per_pass == 1
+    # k = 4 for 4-byte symbols, >= 8 levels and n >= 2^22; else 1
+    big = 1 << 22
+    for cls in (wt.WaveletMatrix, wt.WaveletTree):
+        with cls(big, 1 << 20, 4) as m:
+            assert m.info().levels_per_pass == 4
+        with cls(big - 1, 1 << 20, 4) as m:
+            assert m.info().levels_per_pass == 1
+        with cls(big, 100, 4) as m:
+            assert m.info().levels_per_pass == 1
+        with cls(big, 256, 1) as m:
+            assert m.info().levels_per_pass == 1
 
 
-def test_one_level_schedule_wide_matrix(wt):
-    # the one-level schedule stays covered where the library picks k = 4
-    for kind in ("uniform", "zipf", "runs"):
-        S = synth.pattern(kind, 5 * 4096 + 3, 70000, 4, seed=3)
-        check(wt, S, 70000, "matrix", 1)
+def test_library_choice_at_scale(wt):
+    # the default schedule of a 4-byte build at n = 2^22 + 5 (k = 4), both shapes
+    S, sigma = synth.config3(n=(1 << 22) + 5)
+    check(wt, S, sigma, "tree", 4)
+    check(wt, S, sigma, "matrix", 4)
+    with wt.WaveletTree(S.size, sigma, 4) as t:
+        assert t.info().levels_per_pass == 4
