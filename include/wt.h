@@ -172,6 +172,18 @@ int wt_build_host(wt_tree *tree, const void *h_seq, uint32_t *h_bits, uint64_t *
                   void *stream);
 
 /*
+ * wt_build_host without the final synchronisation: enqueues the copy in, the
+ * build and the copies out, and returns.  Work enqueued later on `stream`
+ * (including the next build of this tree) runs after the copies out;
+ * wt_sync(tree) waits for all of it and returns the build status.  h_seq,
+ * h_bits and h_rank must stay valid until then.  Builds of different trees
+ * on different streams overlap: one build's copies with another's kernels.
+ * Errors: as wt_build_host, but device-side errors only through wt_sync.
+ */
+int wt_build_host_async(wt_tree *tree, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
+                        void *stream);
+
+/*
  * Wavelet matrix (Section 7).  Allocates like wt_create, without the
  * histogram, node tables and d_node_start, for a wt_tree of shape
  * WT_SHAPE_MATRIX.  Every other call taking a wt_tree (wt_rebuild,

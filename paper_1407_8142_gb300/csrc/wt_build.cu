@@ -443,6 +443,7 @@ void release(wt_tree *t) {
     cudaStreamDestroy(t->copy_stream);
     for (uint32_t l = 0; l < kMaxLevels; ++l)
       if (t->level_ev[l]) cudaEventDestroy(t->level_ev[l]);
+    if (t->copy_done) cudaEventDestroy(t->copy_done);
   }
   if (t->ev) {
     for (uint32_t i = 0; i < 2 * kMaxProfiled; ++i)
@@ -662,8 +663,8 @@ int wt_sync(wt_tree *t) {
   return t->sticky_error;
 }
 
-int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
-                  void *stream) {
+int wt_build_host_async(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
+                        void *stream) {
   if (!t || (!h_seq && t->n) || t->owner) return WT_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!t->d_in_host) WT_CUDA(cudaMalloc(&t->d_in_host, t->buf_bytes));
@@ -671,6 +672,7 @@ int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_r
   const bool copy_out = t->n && L && (h_bits || h_rank);
   if (copy_out && !t->copy_stream) {
     WT_CUDA(cudaStreamCreateWithFlags(&t->copy_stream, cudaStreamNonBlocking));
+    WT_CUDA(cudaEventCreateWithFlags(&t->copy_done, cudaEventDisableTiming));
     for (uint32_t l = 0; l < L; ++l) WT_CUDA(cudaEventCreateWithFlags(&t->level_ev[l], cudaEventDisableTiming));
   }
   if (t->n) WT_CUDA(cudaMemcpyAsync(t->d_in_host, h_seq, t->n * t->sb, cudaMemcpyHostToDevice, st));
@@ -690,8 +692,17 @@ int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_r
         WT_CUDA(cudaMemcpyAsync(h_rank + (uint64_t)l * (t->NB + 1), t->d_rank + (uint64_t)l * (t->NB + 1),
                                 (t->NB + 1) * 8, cudaMemcpyDeviceToHost, t->copy_stream));
     }
-    WT_CUDA(cudaStreamSynchronize(t->copy_stream));
+    // later work on `stream` (the next build, wt_sync) waits for the copies
+    WT_CUDA(cudaEventRecord(t->copy_done, t->copy_stream));
+    WT_CUDA(cudaStreamWaitEvent(st, t->copy_done, 0));
   }
+  return WT_OK;
+}
+
+int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_rank,
+                  void *stream) {
+  const int rc = wt_build_host_async(t, h_seq, h_bits, h_rank, stream);
+  if (rc) return rc;
   return wt_sync(t);
 }
 

@@ -74,6 +74,7 @@ struct wt_tree {
   // soon as the pass that writes them is done (level_ev, recorded after it)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t level_ev[wtk::kMaxLevels] = {};
+  cudaEvent_t copy_done = nullptr;  // recorded after the last copy out
   bool record_levels = false;
 
   bool profile = false;

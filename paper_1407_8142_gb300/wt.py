@@ -67,6 +67,7 @@ SIGNATURES = {
     "wt_build": (ctypes.c_int, [P, U64, U32, U32, P, ctypes.POINTER(P)]),
     "wt_build_ex": (ctypes.c_int, [P, U64, U32, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
     "wt_build_host": (ctypes.c_int, [P, P, P, P, P]),
+    "wt_build_host_async": (ctypes.c_int, [P, P, P, P, P]),
     "wt_matrix_create": (ctypes.c_int, [U64, U32, U32, ctypes.POINTER(Config), ctypes.POINTER(P)]),
     "wt_matrix_build": (ctypes.c_int, [P, U64, U32, U32, ctypes.POINTER(Config), P, ctypes.POINTER(P)]),
     "wt_sync": (ctypes.c_int, [P]),
@@ -199,6 +200,11 @@ def wt_matrix_build(d_seq: int, n: int, sigma: int, symbol_bytes: int, stream=No
 def wt_build_host(tree: int, h_seq: int, h_bits: int | None, h_rank: int | None,
                   stream=None) -> int:
     return load().wt_build_host(tree, h_seq, h_bits, h_rank, _stream_ptr(stream))
+
+
+def wt_build_host_async(tree: int, h_seq: int, h_bits: int | None, h_rank: int | None,
+                        stream=None) -> int:
+    return load().wt_build_host_async(tree, h_seq, h_bits, h_rank, _stream_ptr(stream))
 
 
 def wt_sync(tree: int) -> int:

@@ -164,6 +164,36 @@ def test_host_path_matches_device_path(wt):
         assert np.array_equal(rank, ref["rank"])
 
 
+@pytest.mark.parametrize("shape", ["tree", "matrix"])
+def test_host_path_async_two_trees(wt, shape):
+    # wt_build_host_async on two trees and two streams, three rounds, no
+    # synchronisation in between: every build's copies out match the oracle
+    import torch
+    n, sigma = 5 * 8192 + 7, 256
+    inputs = [synth.uniform(n, sigma, 1, seed=11), synth.zipf(n, sigma, 1.0, 1, seed=12)]
+    ref_of = serialwt.matrix_build if shape == "matrix" else serialwt.build
+    refs = [ref_of(S, sigma) for S in inputs]
+    cls = wt.WaveletMatrix if shape == "matrix" else wt.WaveletTree
+    with cls(n, sigma, 1) as a, cls(n, sigma, 1) as b:
+        inf = a.info()
+        L, W, NB = inf.levels, inf.words_per_level, inf.blocks
+        hs = [torch.from_numpy(S).pin_memory() for S in inputs]
+        outs = [(torch.zeros(L * W, dtype=torch.int32).pin_memory(),
+                 torch.zeros(L * (NB + 1), dtype=torch.int64).pin_memory()) for _ in range(2)]
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for _ in range(3):
+            for k, t in enumerate((a, b)):
+                rc = wt.wt_build_host_async(t.handle, hs[k].data_ptr(), outs[k][0].data_ptr(),
+                                            outs[k][1].data_ptr(), streams[k])
+                assert rc == wt.WT_OK
+        assert a.sync() == wt.WT_OK and b.sync() == wt.WT_OK
+        for k in range(2):
+            bits = outs[k][0].numpy().view(np.uint32).reshape(L, W)
+            rank = outs[k][1].numpy().view(np.uint64).reshape(L, NB + 1)
+            assert np.array_equal(bits, refs[k]["bits"])
+            assert np.array_equal(rank, refs[k]["rank"])
+
+
 @pytest.mark.parametrize("sigma,b,n", [(1, 1, 100), (2, 1, 1000), (5, 1, 3001), (256, 1, 20000),
                                        (65536, 2, 9000), (1 << 20, 4, 9000), (1000, 4, 50000)])
 def test_queries(wt, sigma, b, n):
