@@ -55,6 +55,10 @@ constexpr uint32_t kFWarps = kFThreads / 32;
 
 template <int SB>
 struct FGeom {
+  // 4-byte symbols: one tile buffer, copied after each tile (the smaller
+  // footprint lets four CTAs share an SM, and their work covers the copy);
+  // narrower symbols: two, the next tile's copy overlapping this one
+  static constexpr int DEPTH = SB == 4 ? 1 : 2;
   static constexpr uint32_t V = 32;  // rows per warp = symbols per thread (tiles of 8192)
   static constexpr uint32_t TS = kFThreads * V;       // symbols per tile
   static constexpr uint32_t NWD = TS / 32;            // bit words per tile and level
@@ -63,7 +67,7 @@ struct FGeom {
 template <int SB, int K>
 __host__ __device__ constexpr uint32_t fused_smem_bytes() {
   using G = FGeom<SB>;
-  return 2u * G::TS * SB                 // two tile buffers (TMA); the rounds run in place
+  return G::DEPTH * G::TS * SB          // tile buffers (TMA); the rounds run in place
          + 4u * (G::NWD + 2)             // round bits, a zero word at each end
          + 8u * G::NWD                   // per row: {bit word, ones before it within its warp}
          + 4u * kFWarps                  // ones per warp
@@ -157,16 +161,16 @@ __device__ __forceinline__ void round_split(Sym *X, const uint2 *wp, uint32_t x0
 }
 
 template <int SB, int K>
-__global__ void __launch_bounds__(kFThreads, 3) k_fused(FusedArgs a) {
+__global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs a) {
   using G = FGeom<SB>;
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t V = G::V, TS = G::TS, NWD = G::NWD;
   constexpr uint32_t D = 1u << K, NH = 2u << K;
   extern __shared__ __align__(128) uint8_t smem[];
-  TilePipe<SB, TS / 32> pipe;  // double buffer, tiles of TS symbols, tickets two ahead
+  TilePipe<SB, TS / 32, G::DEPTH> pipe;  // tiles of TS symbols, tickets two ahead
   pipe.sIn0 = smem;
-  pipe.sIn1 = smem + TS * SB;
-  uint32_t *const sBits = reinterpret_cast<uint32_t *>(smem + 2 * TS * SB);
+  pipe.sIn1 = smem + (G::DEPTH - 1) * TS * SB;
+  uint32_t *const sBits = reinterpret_cast<uint32_t *>(smem + G::DEPTH * TS * SB);
   uint2 *const sWP = reinterpret_cast<uint2 *>(sBits + NWD + 2);  // NWD + 2 words: 8-byte aligned
   uint32_t *const sWarpOnes = reinterpret_cast<uint32_t *>(sWP + NWD);
   uint32_t *const sCnt = sWarpOnes + kFWarps;  // per heap slot
@@ -392,6 +396,7 @@ __global__ void __launch_bounds__(kFThreads, 3) k_fused(FusedArgs a) {
     }
     if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
     __syncthreads();
+    if (G::DEPTH == 1 && tid == 0) pipe.after_tile(nxt);
     pre = pre_next;
   }
 }
@@ -454,14 +459,23 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
   if (nodes) __syncthreads();
   const uint32_t full = (nv * SB) >> 4;  // whole 16-byte chunks
   uint32_t mx = 0;
-  for (uint32_t q = tid; q < full; q += kFThreads) {
-    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(base) + q);
-    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+  // all of this thread's loads are issued before any is counted
+  constexpr uint32_t CH = TS * SB / 16 / kFThreads;
+  uint4 w[CH];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+  for (uint32_t c = 0; c < CH; ++c) {
+    const uint32_t q = tid + c * kFThreads;
+    w[c] = q < full ? __ldg(reinterpret_cast<const uint4 *>(base) + q) : make_uint4(0, 0, 0, 0);
+  }
+#pragma unroll
+  for (uint32_t c = 0; c < CH; ++c) {
+    if (tid + c * kFThreads >= full) break;
+    const uint32_t words[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
 #pragma unroll
       for (int e = 0; e < 4 / SB; ++e) {
-        const uint32_t raw = SB == 4 ? words[c] : (words[c] >> (8 * SB * e)) & ((1u << (8 * SB)) - 1u);
+        const uint32_t raw = SB == 4 ? words[k] : (words[k] >> (8 * SB * e)) & ((1u << (8 * SB)) - 1u);
         mx = max(mx, raw);
         sH[(((raw & lmask) >> dsh) & (D - 1)) * kFThreads + tid] += 1u;
         if (nodes) count_node<K>(a, sNC, raw & lmask, p0, keyed);
