@@ -64,15 +64,18 @@ struct FGeom {
   static constexpr uint32_t NWD = TS / 32;            // bit words per tile and level
 };
 
-template <int SB, int K>
+constexpr uint32_t kFewNodes = 16;  // tree tiles over fewer nodes write per-(class, node) runs
+
+template <int SB, int K, bool MATRIX>
 __host__ __device__ constexpr uint32_t fused_smem_bytes() {
   using G = FGeom<SB>;
   return G::DEPTH * G::TS * SB          // tile buffers (TMA); the rounds run in place
          + 4u * (G::NWD + 2)             // round bits, a zero word at each end
          + 8u * G::NWD                   // per row: {bit word, ones before it within its warp}
          + 4u * kFWarps                  // ones per warp
-         + 4u * 6u * (2u << K)           // per class: count, offset, start, prefix, matrix base,
-                                         // start minus offset
+         + 4u * 6u * (2u << K)           // per class: count, offset, start, prefix, matrix base, start - offset
+         + (MATRIX ? 0u : 4u * kFewNodes * ((1u << K) * 2u + (2u << K) * 3u))  // per node: digit counts,
+                                         // start - offset; per (class, node) run: length, offset, start
          + 4u * 8u                       // zeros per round, flags
          + 72u;                          // mbarriers, tickets
 }
@@ -160,12 +163,12 @@ __device__ __forceinline__ void round_split(Sym *X, const uint2 *wp, uint32_t x0
   }
 }
 
-template <int SB, int K>
+template <int SB, int K, bool MATRIX>
 __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs a) {
   using G = FGeom<SB>;
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t V = G::V, TS = G::TS, NWD = G::NWD;
-  constexpr uint32_t D = 1u << K, NH = 2u << K;
+  constexpr uint32_t D = 1u << K, NH = 2u << K, SP = kFewNodes;
   extern __shared__ __align__(128) uint8_t smem[];
   TilePipe<SB, TS / 32, G::DEPTH> pipe;  // tiles of TS symbols, tickets two ahead
   pipe.sIn0 = smem;
@@ -179,9 +182,15 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
   uint32_t *const sGx = sGb + NH;
   uint32_t *const sMb = sGx + NH;
   uint32_t *const sDelta = sMb + NH;  // digit d: start of its run in T_{l+K} minus its offset in the tile
-  uint32_t *const sZt = sDelta + NH;  // K words
-  uint32_t *const sFlag = sZt + 4;   // [0] tile within one node, [1] that node
-  pipe.bar = reinterpret_cast<uint64_t *>(smem + ((fused_smem_bytes<SB, K>() - 72u + 7u) & ~7u));
+  // tiles over a few nodes (tree only): node j = node - first node of the tile
+  uint32_t *const sCntN = sDelta + NH;                        // [j][digit] symbols
+  uint32_t *const sDeltaN = sCntN + (MATRIX ? 0 : SP * D);    // [j][digit] start - offset in T_{l+K}
+  uint32_t *const sRunLen = sDeltaN + (MATRIX ? 0 : SP * D);  // [class][j] run of node j in the class
+  uint32_t *const sRunOff = sRunLen + (MATRIX ? 0 : NH * SP);
+  uint32_t *const sRunG = sRunOff + (MATRIX ? 0 : NH * SP);
+  uint32_t *const sZt = sRunG + (MATRIX ? 0 : NH * SP);       // K words
+  uint32_t *const sFlag = sZt + 4;  // [0] nodes of the tile: 1, few (< SP) = 2, more = 0; [1] first node; [2] span
+  pipe.bar = reinterpret_cast<uint64_t *>(smem + ((fused_smem_bytes<SB, K, MATRIX>() - 72u + 7u) & ~7u));
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
   pipe.in = a.in;
   pipe.in_padded = a.in_padded;
@@ -191,12 +200,12 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lmask = (1u << a.L) - 1u;  // L <= 26
-  const bool matrix = a.matrix != 0;
+  const uint32_t ps = a.L - a.level;        // node of a symbol: its top l bits
   if (tid == 0) {
     sBits[0] = 0;
     sBits[NWD + 1] = 0;
   }
-  if (matrix && tid < NH - 1) {
+  if (MATRIX && tid < NH - 1) {
     // start of each class of granularity >= 1 in T_{l+i}: the classes whose
     // bits, read from the last to the first, are smaller come first
     const uint32_t h = tid, i = gran_of(h), c = h + 1 - (1u << i);
@@ -244,21 +253,36 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
     // ---- class tables of the tile
     if (tid < D) sCnt[D - 1 + tid] = pre;
     else if (tid < 2 * D) sGx[D - 1 + (tid - D)] = pre;
-    if (tid == 2 * D) {
-      uint32_t one = 1, node = 0;
-      if (!matrix && a.level) {
-        const uint32_t ps = a.L - a.level;
-        node = ((uint32_t)X[0] & lmask) >> ps;
-        one = node == (((uint32_t)X[nv - 1] & lmask) >> ps);
+    if (!MATRIX) {
+      for (uint32_t i = tid; i < SP * D; i += kFThreads) sCntN[i] = 0;
+      if (tid == 2 * D) {
+        // nodes of the tile (T_l is ordered by node)
+        uint32_t kind = 1, node = 0, span = 0;
+        if (a.level) {
+          node = ((uint32_t)X[0] & lmask) >> ps;
+          span = (((uint32_t)X[nv - 1] & lmask) >> ps) - node;
+          kind = span == 0 ? 1u : span < SP ? 2u : 0u;
+        }
+        sFlag[0] = kind;
+        sFlag[1] = node;
+        sFlag[2] = span;
       }
-      sFlag[0] = one;
-      sFlag[1] = node;
     }
     __syncthreads();
+    const uint32_t kind = MATRIX ? 1u : sFlag[0];
+    const bool single = kind == 1, few = kind == 2;
+    const uint32_t p0 = MATRIX ? 0u : sFlag[1], span = MATRIX ? 0u : sFlag[2];
+    if (few) {  // digits of every node of the tile
+      const uint32_t dsh = a.L - a.level - K;
+      for (uint32_t x = tid; x < nv; x += kFThreads) {
+        const uint32_t v = (uint32_t)X[x] & lmask;
+        atomicAdd(&sCntN[((v >> ps) - p0) * D + ((v >> dsh) & (D - 1))], 1u);
+      }
+    }
     if (tid < D - 1) {  // coarser classes: sums over their digits
-      const uint32_t h = tid, gi = gran_of(h), c = h + 1 - (1u << gi), span = 1u << (K - gi);
+      const uint32_t h = tid, gi = gran_of(h), c = h + 1 - (1u << gi), sp = 1u << (K - gi);
       uint32_t cn = 0, gx = 0;
-      for (uint32_t d = c * span; d < (c + 1) * span; ++d) {
+      for (uint32_t d = c * sp; d < (c + 1) * sp; ++d) {
         cn += sCnt[D - 1 + d];
         gx += sGx[D - 1 + d];
       }
@@ -266,7 +290,6 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
       sGx[h] = gx;
     }
     __syncthreads();
-    const bool single = sFlag[0] != 0;
     if (tid < NH - 1) {
       const uint32_t h = tid, gi = gran_of(h), c = h + 1 - (1u << gi);
       uint32_t off = 0;
@@ -278,14 +301,20 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
       sOff[h] = off;
       uint32_t gb = 0;
       if (gi && (gi < K || a.out)) {  // the last pass writes no T_{l+K}
-        if (matrix) gb = sMb[h] + sGx[h];
-        else if (single) {
-          const uint32_t m = a.level + gi;
-          gb = __ldg(&a.F[(1u << m) - 2u + ((sFlag[1] << gi) | c)]) + sGx[h];
-        }
+        if (MATRIX) gb = sMb[h] + sGx[h];
+        else if (single) gb = __ldg(&a.F[(1u << (a.level + gi)) - 2u + ((p0 << gi) | c)]) + sGx[h];
       }
       sGb[h] = gb;
       if (gi == K) sDelta[c] = gb - off;
+    }
+    if (few) {  // symbols of node j in class h (granularity >= 1)
+      for (uint32_t t = tid; t < (NH - 2) * (span + 1); t += kFThreads) {
+        const uint32_t h = 1 + t / (span + 1), j = t % (span + 1);
+        const uint32_t gi = gran_of(h), c = h + 1 - (1u << gi), sp = 1u << (K - gi);
+        uint32_t cn = 0;
+        for (uint32_t d = c * sp; d < (c + 1) * sp; ++d) cn += sCntN[j * D + d];
+        sRunLen[h * SP + j] = cn;
+      }
     }
     if (tid < K) {  // zeros of round tid: classes of the next granularity ending in 0
       uint32_t z = 0;
@@ -293,6 +322,26 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
       sZt[tid] = z;
     }
     __syncthreads();
+    if (few) {
+      // node j's run of class h starts after the runs of nodes < j in the
+      // class segment; its symbols go to F of node j's child plus G of the
+      // class plus their place in the class segment
+      for (uint32_t t = tid; t < (NH - 2) * (span + 1); t += kFThreads) {
+        const uint32_t h = 1 + t / (span + 1), j = t % (span + 1);
+        const uint32_t gi = gran_of(h), c = h + 1 - (1u << gi);
+        uint32_t before = 0;
+        for (uint32_t j2 = 0; j2 < j; ++j2) before += sRunLen[h * SP + j2];
+        sRunOff[h * SP + j] = sOff[h] + before;
+        uint32_t g = 0;
+        if (sRunLen[h * SP + j] && (gi < K || a.out)) {
+          const uint32_t f = __ldg(&a.F[(1u << (a.level + gi)) - 2u + (((p0 + j) << gi) | c)]) + sGx[h];
+          g = f + before;
+          if (gi == K) sDeltaN[j * D + c] = f - sOff[h];
+        }
+        sRunG[h * SP + j] = g;
+      }
+      __syncthreads();
+    }
 
     const bool full = nv == TS;
     uint32_t v[V];
@@ -331,9 +380,17 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
           const uint32_t len = sCnt[h];
           if (len && sGb[h] + (uint64_t)len <= a.n) warp_bit_run(sBits, sOff[h], row, sGb[h], len);
         }
-      } else {
-        // a tile over several nodes: destinations of each row in T_{l+i},
-        // one run per stretch of consecutive destinations
+      } else if (few) {
+        // one run per (class, node)
+        const uint32_t runs = (1u << i) * (span + 1);
+        for (uint32_t t = warp; t < runs; t += kFWarps) {
+          const uint32_t h = (1u << i) - 1 + t / (span + 1), j = t % (span + 1);
+          const uint32_t len = sRunLen[h * SP + j], g = sRunG[h * SP + j];
+          if (len && g + (uint64_t)len <= a.n) warp_bit_run(sBits, sRunOff[h * SP + j], row, g, len);
+        }
+      } else if (!MATRIX) {
+        // a tile over many nodes: destinations of each row in T_{l+i}, one
+        // run per stretch of consecutive destinations
 #pragma unroll
         for (uint32_t r = 0; r < V; ++r) {
           const uint32_t x = xw + 32 * r + lane;
@@ -378,14 +435,16 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
       Sym *const out = reinterpret_cast<Sym *>(a.out);
       const uint32_t m = a.level + K;
       const uint32_t shK = a.L - m;
-      if (single) {
-        // the class of a symbol gives its destination: x + (start - offset)
+      if (single || few) {
+        // the class (and node) of a symbol gives its destination: x + (start - offset)
+        const uint32_t *delta = single ? sDelta : sDeltaN;
         for (uint32_t x = tid; x < nv; x += kFThreads) {
           const uint32_t s = X[x];
-          const uint32_t dest = x + sDelta[(s >> shK) & (D - 1)];
+          const uint32_t j = few ? (s >> ps) - p0 : 0u;
+          const uint32_t dest = x + delta[j * D + ((s >> shK) & (D - 1))];
           if (dest < a.n) out[dest] = (Sym)s;
         }
-      } else {
+      } else if (!MATRIX) {
         for (uint32_t x = tid; x < nv; x += kFThreads) {
           const uint32_t s = X[x];
           const uint32_t h = D - 1 + ((s >> shK) & (D - 1));
@@ -674,10 +733,10 @@ int last_error() {
   return e == cudaSuccess ? WT_OK : cuda_err(e);
 }
 
-template <int SB, int K>
+template <int SB, int K, bool MATRIX>
 int launch_k(wt_tree *t, cudaStream_t st, const FusedArgs &a) {
-  auto kern = k_fused<SB, K>;
-  constexpr uint32_t sm = fused_smem_bytes<SB, K>();
+  auto kern = k_fused<SB, K, MATRIX>;
+  constexpr uint32_t sm = fused_smem_bytes<SB, K, MATRIX>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return cuda_err(e);
   int occ = 0;
@@ -692,15 +751,20 @@ int launch_k(wt_tree *t, cudaStream_t st, const FusedArgs &a) {
   return last_error();
 }
 
-template <int SB>
-int launch_sb(wt_tree *t, cudaStream_t st, const FusedArgs &a, uint32_t K) {
+template <int SB, bool MATRIX>
+int launch_shape(wt_tree *t, cudaStream_t st, const FusedArgs &a, uint32_t K) {
   switch (K) {
-    case 1: return launch_k<SB, 1>(t, st, a);
-    case 2: return launch_k<SB, 2>(t, st, a);
-    case 3: return launch_k<SB, 3>(t, st, a);
-    case 4: return launch_k<SB, 4>(t, st, a);
+    case 1: return launch_k<SB, 1, MATRIX>(t, st, a);
+    case 2: return launch_k<SB, 2, MATRIX>(t, st, a);
+    case 3: return launch_k<SB, 3, MATRIX>(t, st, a);
+    case 4: return launch_k<SB, 4, MATRIX>(t, st, a);
   }
   return WT_ERR_ARG;
+}
+
+template <int SB>
+int launch_sb(wt_tree *t, cudaStream_t st, const FusedArgs &a, uint32_t K) {
+  return a.matrix ? launch_shape<SB, true>(t, st, a, K) : launch_shape<SB, false>(t, st, a, K);
 }
 
 template <int SB>
