@@ -209,3 +209,11 @@ def test_library_choice_at_scale(wt):
     check(wt, S, sigma, "matrix", 4)
     with wt.WaveletTree(S.size, sigma, 4) as t:
         assert t.info().levels_per_pass == 4
+
+
+@pytest.mark.parametrize("shape", ["tree", "matrix"])
+def test_few_nodes_per_tile_at_scale(wt, shape):
+    # n = 2^23 + 13 over 2^16 symbols: at level 12 nodes hold ~2^11 symbols,
+    # so 8192-symbol tiles span a few nodes (one run per class and node)
+    S = synth.zipf((1 << 23) + 13, 1 << 16, 1.0, 4, seed=21)
+    check(wt, S, 1 << 16, shape, 4)
