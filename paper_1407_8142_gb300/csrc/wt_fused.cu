@@ -33,9 +33,11 @@
 // tile's first ballot words, in place.
 //
 // A tile whose symbols lie in one node (all tiles of the matrix) writes one
-// run per class.  A tile that spans nodes writes, per row of 32 image
-// positions, one run per stretch of consecutive destinations, with F looked
-// up per symbol.
+// run per class.  A tile over a few nodes counts its symbols per (node,
+// digit) and writes one run per class and node (within a class the nodes'
+// symbols follow each other in T_l order).  A tile over many nodes writes,
+// per row of 32 image positions, one run per stretch of consecutive
+// destinations, with F looked up per symbol.
 //
 // Directories are a separate pass over the finished rows (k_dir).
 #include <algorithm>
@@ -787,7 +789,7 @@ uint32_t fused_tile_symbols(uint32_t symbol_bytes) {
   return symbol_bytes == 4 ? FGeom<4>::TS : symbol_bytes == 2 ? FGeom<2>::TS : FGeom<1>::TS;
 }
 
-uint32_t fused_tables_blocks(uint32_t L, uint32_t K) { return fused_tables_blocks_range(1, L - 1, K); }
+uint32_t fused_tables_blocks(uint32_t L, uint32_t K) { return L >= 2 ? fused_tables_blocks_range(1, L - 1, K) : 0u; }
 
 uint32_t fused_tables_blocks_range(uint32_t m_lo, uint32_t m_hi, uint32_t K) {
   uint32_t nb = 0;

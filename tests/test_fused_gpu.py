@@ -217,3 +217,19 @@ def test_few_nodes_per_tile_at_scale(wt, shape):
     # so 8192-symbol tiles span a few nodes (one run per class and node)
     S = synth.zipf((1 << 23) + 13, 1 << 16, 1.0, 4, seed=21)
     check(wt, S, 1 << 16, shape, 4)
+
+
+def test_one_symbol_alphabet(wt):
+    # sigma = 1 (no levels) with k requested: the one-level schedule's
+    # pre-pass and node starts, nothing else
+    for n in (0, 1, 5000):
+        S = np.zeros(n, dtype=np.uint8)
+        with wt.WaveletTree(n, 1, 1, levels_per_pass=4) as t:
+            t.build(S)
+            assert t.sync() == wt.WT_OK
+            out = t.to_host()
+            assert out["L"] == 0
+            assert int(out["node_start"][-1]) == n
+        with wt.WaveletMatrix(n, 1, 1, levels_per_pass=3) as m:
+            m.build(S)
+            assert m.sync() == wt.WT_OK
