@@ -358,7 +358,7 @@ int run_build_fused(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_
     if ((rc = fused_count(t, st, in, l, K, l == 0))) return rc;
     ln.after();
     ln.before(kTileScan);
-    if ((rc = fused_scan(t, st, K))) return rc;
+    if ((rc = fused_scan(t, st, l, K))) return rc;
     ln.after();
     if (tree) {
       if ((rc = launch_hist_scan(ln, 1u << top))) return rc;

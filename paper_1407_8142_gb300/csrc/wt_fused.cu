@@ -468,7 +468,9 @@ struct CountArgs {
   uint32_t n, L, level, NT;
   uint32_t sigma;      // range check of the input symbols (first pass), 0 = none
   uint32_t *tcnt;      // digit d of tile t at tcnt[d * NT + t]
-  uint32_t *ncount;    // tree: symbols per node of level level+K (zeroed), else null
+  uint32_t *ncount;    // tree: symbols per node of level level+K (zeroed), else null;
+                       // tile t adds to copy t & rep_mask (2^top counters each)
+  uint32_t rep_mask, top;
   int *err;
 };
 
@@ -479,11 +481,11 @@ constexpr uint32_t kSpanKeyed = 32;  // tiles over fewer nodes count them in sha
 // when the tile spans fewer than kSpanKeyed nodes, else straight to global
 // memory (such tiles hold many small nodes, so there is no hot counter).
 template <uint32_t K>
-__device__ __forceinline__ void count_node(const CountArgs &a, uint32_t *sNC, uint32_t v, uint32_t p0,
-                                           bool keyed) {
+__device__ __forceinline__ void count_node(const CountArgs &a, uint32_t *nc, uint32_t *sNC, uint32_t v,
+                                           uint32_t p0, bool keyed) {
   const uint32_t q = v >> (a.L - a.level - K);
   if (keyed) atomicAdd(&sNC[q - (p0 << K)], 1u);
-  else atomicAdd(&a.ncount[q], 1u);
+  else atomicAdd(&nc[q], 1u);
 }
 
 // Symbols of each digit in each tile of T_l (tiles of the k-level pass).
@@ -514,6 +516,9 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
   const uint32_t p0 = tree_node ? (((uint32_t)syms[0] & lmask) >> ps) : 0u;
   const uint32_t p1 = tree_node ? (((uint32_t)syms[nv - 1] & lmask) >> ps) : 0u;
   const bool nodes = a.ncount != nullptr && p0 != p1;  // count nodes per symbol
+  // this tile's copy of the node counters: the tiles of one large node
+  // would otherwise all add to the same 2^K counters
+  uint32_t *const nc = a.ncount ? a.ncount + ((size_t)(tile & a.rep_mask) << a.top) : nullptr;
   const bool keyed = p1 - p0 < kSpanKeyed;
   if (nodes && keyed)
     for (uint32_t i = tid; i < kSpanKeyed * D; i += kFThreads) sNC[i] = 0;
@@ -539,7 +544,7 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
         const uint32_t raw = SB == 4 ? words[k] : (words[k] >> (8 * SB * e)) & ((1u << (8 * SB)) - 1u);
         mx = max(mx, raw);
         sH[(((raw & lmask) >> dsh) & (D - 1)) * kFThreads + tid] += 1u;
-        if (nodes) count_node<K>(a, sNC, raw & lmask, p0, keyed);
+        if (nodes) count_node<K>(a, nc, sNC, raw & lmask, p0, keyed);
       }
     }
   }
@@ -547,7 +552,7 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
     const uint32_t raw = syms[x];
     mx = max(mx, raw);
     sH[(((raw & lmask) >> dsh) & (D - 1)) * kFThreads + tid] += 1u;
-    if (nodes) count_node<K>(a, sNC, raw & lmask, p0, keyed);
+    if (nodes) count_node<K>(a, nc, sNC, raw & lmask, p0, keyed);
   }
   if (a.sigma && mx >= a.sigma) latch_error(a.err, WT_ERR_SYMBOL);
   __syncthreads();
@@ -557,12 +562,12 @@ __global__ void __launch_bounds__(kFThreads) k_tilecount(CountArgs a) {
     s = __reduce_add_sync(0xFFFFFFFFu, s);
     if (lane == 0) {
       a.tcnt[(uint64_t)d * a.NT + tile] = s;
-      if (a.ncount && !nodes && s) atomicAdd(&a.ncount[(p0 << K) | d], s);  // one node
+      if (a.ncount && !nodes && s) atomicAdd(&nc[(p0 << K) | d], s);  // one node
     }
   }
   if (nodes && keyed) {
     for (uint32_t i = tid; i < kSpanKeyed * D && (i >> K) <= p1 - p0; i += kFThreads)
-      if (sNC[i]) atomicAdd(&a.ncount[(p0 << K) + i], sNC[i]);
+      if (sNC[i]) atomicAdd(&nc[(p0 << K) + i], sNC[i]);
   }
 }
 
@@ -571,13 +576,22 @@ struct TileScanArgs {
   uint32_t *tpre;      // exclusive prefix over the tiles, per digit
   uint32_t *tot;       // symbols per digit (may be null)
   uint32_t NT;
+  uint32_t *ncount;    // tree: rep copies of nwords node counters, summed into the first
+  uint32_t rep, nwords;
 };
 
-// One CTA per digit: exclusive scan of its NT tile counts.
+// One CTA per digit: exclusive scan of its NT tile counts.  The CTAs also
+// sum the copies of the node counters into the first copy.
 __global__ void __launch_bounds__(1024) k_tilescan(TileScanArgs a) {
   constexpr uint32_t ITEMS = 4, CH = 1024 * ITEMS;
   __shared__ uint32_t s_warp[33];
   const uint32_t d = blockIdx.x, tid = threadIdx.x;
+  if (a.ncount && a.rep > 1)
+    for (uint32_t i = d * 1024 + tid; i < a.nwords; i += gridDim.x * 1024) {
+      uint32_t s = 0;
+      for (uint32_t r = 0; r < a.rep; ++r) s += __ldcg(&a.ncount[(size_t)r * a.nwords + i]);
+      a.ncount[i] = s;
+    }
   const uint32_t *c = a.tcnt + (uint64_t)d * a.NT;
   uint32_t *p = a.tpre + (uint64_t)d * a.NT;
   uint32_t carry = 0;
@@ -802,6 +816,12 @@ uint32_t fused_tables_blocks_range(uint32_t m_lo, uint32_t m_hi, uint32_t K) {
 
 uint32_t fused_dir_chunks(uint64_t NB) { return (uint32_t)((NB + kScanChunk - 1) / kScanChunk); }
 
+// Copies of the tree's node counters of level `top`: as many as fit in the
+// 2^L-word counter array, at most 256.
+uint32_t node_copies(const wt_tree *t, uint32_t top) {
+  return t->shape == WT_SHAPE_TREE ? std::min<uint32_t>(256u, 1u << (t->L - top)) : 1u;
+}
+
 int fused_count(wt_tree *t, cudaStream_t st, const uint8_t *in, uint32_t level, uint32_t K, bool check) {
   CountArgs a;
   a.in = in;
@@ -812,7 +832,14 @@ int fused_count(wt_tree *t, cudaStream_t st, const uint8_t *in, uint32_t level, 
   a.sigma = check ? t->sigma : 0u;
   a.tcnt = t->d_fcount;
   a.ncount = t->shape == WT_SHAPE_TREE ? t->d_hist : nullptr;
+  a.top = level + K;
+  const uint32_t rep = node_copies(t, a.top);
+  a.rep_mask = rep - 1;
   a.err = reinterpret_cast<int *>(t->d_ctrl + kCtrlErr);
+  if (a.ncount && rep > 1) {
+    const cudaError_t e = cudaMemsetAsync(a.ncount, 0, ((size_t)rep << a.top) * 4, st);
+    if (e != cudaSuccess) return cuda_err(e);
+  }
   switch (t->sb) {
     case 1: return launch_count_sb<1>(st, a, K);
     case 2: return launch_count_sb<2>(st, a, K);
@@ -821,12 +848,15 @@ int fused_count(wt_tree *t, cudaStream_t st, const uint8_t *in, uint32_t level, 
   return WT_ERR_ARG;
 }
 
-int fused_scan(wt_tree *t, cudaStream_t st, uint32_t K) {
+int fused_scan(wt_tree *t, cudaStream_t st, uint32_t level, uint32_t K) {
   TileScanArgs a;
   a.tcnt = t->d_fcount;
   a.tpre = t->d_fcount + ((uint64_t)t->NTf << t->fuse_k);
   a.tot = t->shape == WT_SHAPE_MATRIX ? t->d_hist : nullptr;
   a.NT = (uint32_t)t->NTf;
+  a.ncount = t->shape == WT_SHAPE_TREE ? t->d_hist : nullptr;
+  a.rep = node_copies(t, level + K);
+  a.nwords = 1u << (level + K);
   k_tilescan<<<1u << K, 1024, 0, st>>>(a);
   return last_error();
 }

@@ -23,7 +23,7 @@ uint32_t fused_dir_chunks(uint64_t NB);
 // counts of level level+K into d_hist (zeroed by the caller); then their
 // exclusive scan over the tiles (and, for the matrix, the digit totals).
 int fused_count(wt_tree *t, cudaStream_t st, const uint8_t *in, uint32_t level, uint32_t K, bool check);
-int fused_scan(wt_tree *t, cudaStream_t st, uint32_t K);
+int fused_scan(wt_tree *t, cudaStream_t st, uint32_t level, uint32_t K);
 
 // One pass over T_level: bits of levels level..level+K-1 and, unless `out`
 // is null (last pass), T_{level+K}.  Rows level+1..level+K-1 of the bitmaps
