@@ -74,7 +74,8 @@ def _time(fn, reps: int) -> float:
 
 
 def tune_single(seq, sigma: int, candidates=(128, 256, 512), reps: int = 3, use_cache: bool = True) -> int:
-    """Best tile_threads for building `seq` (CUDA tensor or numpy array)."""
+    """Best tile_threads for building `seq` (CUDA tensor or numpy array) one
+    level per pass (the CTA size of the k-level passes is fixed)."""
     from . import wt
     t = wt._torch_symbols(seq)
     n, b = t.numel(), t.element_size()
@@ -85,7 +86,7 @@ def tune_single(seq, sigma: int, candidates=(128, 256, 512), reps: int = 3, use_
             return int(hit["tile_threads"])
     times = {}
     for th in candidates:
-        with wt.WaveletTree(n, sigma, b, tile_threads=th) as tree:
+        with wt.WaveletTree(n, sigma, b, tile_threads=th, levels_per_pass=1) as tree:
             times[th] = _time(lambda: tree.build(t), reps)
             if tree.sync() != 0:
                 raise RuntimeError("build failed during autotuning")
