@@ -164,6 +164,21 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
+def theoretical_hbm_gbs(dev=0):
+    """Device-reported peak: memory clock x bus width x 2 (double data rate),
+    GB/s; None where the properties are not reported."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        khz = float(getattr(p, "memory_clock_rate", 0) or 0)
+        bits = float(getattr(p, "memory_bus_width", 0) or 0)
+        if khz <= 0 or bits <= 0:
+            return None
+        return 2.0 * khz * 1e3 * bits / 8.0 / 1e9
+    except Exception:
+        return None
+
+
 def kernel_source_hash() -> str:
     """Hash of the sources the single-build kernels and their launches come
     from (a committed ncu figure is used only while it matches)."""
@@ -351,6 +366,7 @@ def main_ours(args):
             idx += 1
     total_kernel_ms = sum(v[1] for v in per_kind.values())
     peak, peak_kind = measured_hbm_peak()
+    theo = theoretical_hbm_gbs(dev)
     achieved = main_bytes / (main_ms * 1e-3) / 1e9 if main_ms else 0.0
     build_bytes = algorithmic_bytes("prepass", 0, n, sb, L)
     if fused:
@@ -370,6 +386,8 @@ def main_ours(args):
                 "kernel": (f"k_fused ({K} levels per pass: reads T_l once, writes T_(l+{K}) and {K} bitmaps)"
                            if fused else "k_split (per-level split pass)"),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy-based)",
+                "theoretical_gbs": round(theo, 1) if theo else None,
+                "frac_of_theoretical": round(achieved / theo, 4) if theo else None,
                 "algorithmic_bytes_per_launch": main_bytes / max(main_launches, 1),
                 "mean_launch_ms": main_ms / max(main_launches, 1),
                 "time_share": round(main_ms / total_kernel_ms, 4) if total_kernel_ms else None,

@@ -61,3 +61,20 @@ def test_traffic_is_used_only_at_matching_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic() == 1.5e9
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "000000000000")
     assert bench.profiled_traffic() is None
+
+
+def test_theoretical_peak_from_device_properties(monkeypatch):
+    import torch
+
+    class Props:
+        memory_clock_rate = 3996000   # kHz
+        memory_bus_width = 8192       # bits
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev=0: Props())
+    assert bench.theoretical_hbm_gbs(0) == pytest.approx(2 * 3.996e9 * 8192 / 8 / 1e9)
+
+    class Missing:
+        pass
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev=0: Missing())
+    assert bench.theoretical_hbm_gbs(0) is None
