@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import subprocess
 import sys
@@ -235,6 +236,41 @@ def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int, k: in
     return 0.0
 
 
+def host_info():
+    """Cores this process may run on and the host CPU's model name."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "hardware", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return cores, model or platform.machine()
+
+
+def cpu_baseline_sequences(seqs, sigmas, max_seqs: int = 64, budget_s: float = 20.0):
+    """The oracle over the first sequences of a batch or trace, one after the
+    other on one host core (at most max_seqs, or budget_s seconds)."""
+    from oracle import serialwt
+    serialwt.build_oracle()
+    done = symbols = 0
+    t0 = time.perf_counter()
+    for S, sg in zip(seqs, sigmas):
+        serialwt.build(np.ascontiguousarray(S), int(sg))
+        done += 1
+        symbols += int(S.size)
+        if done >= max_seqs or time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores, model = host_info()
+    return {"value": symbols / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} sequences ({symbols} symbols), serialWT, 1 thread, gcc -O2",
+            "seconds": dt, "host_cores": cores, "cpu_model": model}
+
+
 def run_cpu_baseline(S: np.ndarray, sample: int, sigma: int = SIGMA, matrix: bool = False):
     from oracle import serialwt
     sub = np.ascontiguousarray(S[:sample])
@@ -244,9 +280,10 @@ def run_cpu_baseline(S: np.ndarray, sample: int, sigma: int = SIGMA, matrix: boo
     fn(sub, sigma)
     dt = time.perf_counter() - t0
     what = "sequential wavelet matrix" if matrix else "serialWT"
+    cores, model = host_info()
     return {"value": sub.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {sub.size} symbols of the workload ({what}, 1 thread, gcc -O2)",
-            "seconds": dt}
+            "seconds": dt, "host_cores": cores, "cpu_model": model}
 
 
 def main_reference(args):
@@ -631,7 +668,9 @@ def main_batch(args):
             "plain": {"ms": ms_plain, "symbols_per_s": total / (ms_plain * 1e-3),
                       "latency_ms_p50": float(np.percentile(lat_p, 50)), "latency_ms_p99": float(np.percentile(lat_p, 99)),
                       "launches": plain_launches},
-            "speedup": ms_plain / ms_batch, "clocks": clocks.summary()}
+            "speedup": ms_plain / ms_batch, "clocks": clocks.summary(),
+            "cpu_baseline": (None if args.no_cpu_baseline
+                             else cpu_baseline_sequences(host, [sg for _, sg, _ in specs]))}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -761,7 +800,9 @@ def main_serve(args):
                                     "symbols_per_s": plain_symbols / plain_makespan, "makespan_s": plain_makespan,
                                     "latency_ms_p50": 1e3 * float(np.percentile(lat_p, 50)) if lat_p else None,
                                     "latency_ms_p99": 1e3 * float(np.percentile(lat_p, 99)) if lat_p else None},
-            "clocks": clocks.summary()}
+            "clocks": clocks.summary(),
+            "cpu_baseline": (None if args.no_cpu_baseline
+                             else cpu_baseline_sequences(payloads, [r["sigma"] for r in reqs]))}
     print(json.dumps(line), flush=True)
     return 0
 

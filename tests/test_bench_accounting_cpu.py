@@ -78,3 +78,12 @@ def test_theoretical_peak_from_device_properties(monkeypatch):
 
     monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev=0: Missing())
     assert bench.theoretical_hbm_gbs(0) is None
+
+
+def test_cpu_baseline_over_sequences():
+    from paper_1407_8142_gb300 import synth
+    seqs = [synth.uniform(5000 + i, 256, 1, i) for i in range(4)] + [synth.uniform(3000, 65536, 2, 9)]
+    r = bench.cpu_baseline_sequences(seqs, [256] * 4 + [65536], max_seqs=3)
+    assert r["kind"] == "oracle" and r["cores"] == 1
+    assert r["sample"].startswith("first 3 sequences (15003 symbols)")
+    assert r["value"] > 0 and r["host_cores"] >= 1 and r["cpu_model"]
