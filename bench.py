@@ -24,6 +24,7 @@ import platform
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -110,9 +111,12 @@ class ClockSampler:
         self.path = None
 
     def __enter__(self):
+        # samples go to $WT_CLOCKS_DIR (kept for inspection) or a temporary
+        # directory; the JSON line carries their summary
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            d = os.environ.get("WT_CLOCKS_DIR") or tempfile.gettempdir()
+            os.makedirs(d, exist_ok=True)
+            self.path = os.path.join(d, f"clocks_{os.getpid()}_{self.gpu}.csv")
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
