@@ -53,6 +53,10 @@ def test_host_side_argument_checks(lib):
         assert lib.wt_create(n, sigma, b, None, ctypes.byref(out)) == wt.WT_ERR_ARG
     cfg = wt.Config(100, 0, 0, 0)  # tile_threads must be 128/256/512
     assert lib.wt_create(10, 4, 1, ctypes.byref(cfg), ctypes.byref(out)) == wt.WT_ERR_ARG
+    cfg = wt.Config(0, 0, 0, 0, 5)  # at most 4 levels per pass
+    assert lib.wt_create(10, 4, 1, ctypes.byref(cfg), ctypes.byref(out)) == wt.WT_ERR_ARG
+    assert lib.wt_matrix_create(10, 4, 1, ctypes.byref(cfg), ctypes.byref(out)) == wt.WT_ERR_ARG
+    assert lib.wt_build_host_async(None, None, None, None, None) == wt.WT_ERR_ARG
     assert lib.wt_rebuild(None, None, None) == wt.WT_ERR_ARG
     assert lib.wt_sync(None) == wt.WT_ERR_ARG
     assert lib.wt_free(None) == wt.WT_OK
