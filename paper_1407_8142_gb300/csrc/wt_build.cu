@@ -845,8 +845,10 @@ extern "C" int wt_build_noalloc(const void *d_seq, uint64_t n, uint32_t sigma,
                                 uint64_t *d_zeros, uint64_t *d_node_start, int32_t *d_status,
                                 void *stream) {
   if (!(symbol_bytes == 1 || symbol_bytes == 2 || symbol_bytes == 4)) return WT_ERR_ARG;
+  // size limit first, written so that no product can wrap (n < 2^21 here,
+  // hence also n < 2^32 as for wt_create)
+  if (n > kStaticMaxSymbolBytes / symbol_bytes) return WT_ERR_ARG;
   if (sigma == 0 || (uint64_t)sigma > (1ull << (8 * symbol_bytes))) return WT_ERR_ARG;
-  if (n * symbol_bytes > kStaticMaxSymbolBytes) return WT_ERR_ARG;
   const uint32_t L = levels_of(sigma);
   if (L > kStaticMaxLevels) return WT_ERR_ARG;
   if (n && !d_seq) return WT_ERR_ARG;
@@ -897,12 +899,17 @@ extern "C" int wt_build_noalloc(const void *d_seq, uint64_t n, uint32_t sigma,
   t.d_counts = t.d_hist + nbins;
   t.d_status = reinterpret_cast<unsigned long long *>(take(t.status_n * 8));
   if (off > kStaticScratchBytes) return WT_ERR_ARG;
-  // the look-back state is never cleared: every build tags it with a new epoch
+  // every build also tags its look-back entries with a new epoch
   t.build_count = g_static_builds.fetch_add(1) + 1;
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // tickets, error word, histogram and tile counts must start at zero
+  // tickets, error word, histogram and tile counts must start at zero.  The
+  // look-back status words sit at an offset that depends on this call's
+  // sizes, so an earlier call with other sizes may have left symbol bytes
+  // there that happen to decode as a published entry of this build's epoch:
+  // they are cleared on every call (a few KB).
   WT_CUDA(cudaMemsetAsync(t.d_ctrl, 0, t.ctrl_words * 4, st));
+  WT_CUDA(cudaMemsetAsync(t.d_status, 0, t.status_n * 8, st));
   if (n == 0) {
     if (L) {
       WT_CUDA(cudaMemsetAsync(d_rank, 0, (size_t)L * 8, st));

@@ -60,3 +60,15 @@ def test_host_side_argument_checks(lib):
     assert lib.wt_rebuild(None, None, None) == wt.WT_ERR_ARG
     assert lib.wt_sync(None) == wt.WT_ERR_ARG
     assert lib.wt_free(None) == wt.WT_OK
+
+
+def test_noalloc_size_checks_cannot_wrap(lib):
+    """The allocation-free build rejects oversized problems on the host, before
+    any CUDA call, also where n * symbol_bytes would wrap around 2^64."""
+    from paper_1407_8142_gb300 import wt
+    for n, b in (((1 << 21) + 1, 1), ((1 << 20) + 1, 2), ((1 << 19) + 1, 4),
+                 (1 << 32, 1), (1 << 63, 2), ((1 << 62) + 1, 4), ((1 << 64) - 1, 1)):
+        assert lib.wt_build_noalloc(None, n, 4, b, None, None, None, None, None, None) == wt.WT_ERR_ARG
+    # sigma beyond 2^16 (17 levels) is beyond the fixed scratch
+    assert lib.wt_build_noalloc(None, 10, (1 << 16) + 1, 4, None, None, None, None, None,
+                                None) == wt.WT_ERR_ARG

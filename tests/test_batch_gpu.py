@@ -4,11 +4,14 @@ Every tree of a batch must equal, bit for bit, the oracle's output for its
 sequence -- also when trees of different sizes, alphabets and symbol widths
 share the launch, and when the batch is built again.
 """
+import os
+
 import numpy as np
 import pytest
 
 from oracle import serialwt
 from paper_1407_8142_gb300 import synth
+from tests._compare import compare_with_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -25,18 +28,7 @@ def wt():
 
 
 def check_tree(view, S, sigma):
-    ref = serialwt.build(S, sigma)
-    out = view.to_host()
-    assert out["status"] == 0
-    assert np.array_equal(out["bits"], ref["bits"])
-    assert np.array_equal(out["rank"], ref["rank"])
-    assert np.array_equal(out["zeros"], ref["zeros"])
-    E = out["node_start"].astype(np.int64)
-    L = ref["L"]
-    for nid, st, ln in zip(ref["node_id"], ref["node_start"], ref["node_len"]):
-        l = (int(nid) + 1).bit_length() - 1
-        p = int(nid) - ((1 << l) - 1)
-        assert E[p << (L - l)] == int(st) and E[(p + 1) << (L - l)] - E[p << (L - l)] == int(ln)
+    compare_with_oracle(view.to_host(), serialwt.build(S, sigma))
 
 
 def mixed_sequences():
@@ -121,3 +113,44 @@ def test_config4_recipe_reduced(wt):
         assert b.sync() == 0
         for i, (S, sg) in enumerate(seqs):
             check_tree(b.tree(i), S, sg)
+
+
+@pytest.mark.slow
+def test_config4_full_batch_matches_oracle(wt):
+    """The whole batched workload at its recipe size: 4096 sequences with
+    lengths floor(2^U(10, 22)) (about 2e9 symbols), sigma drawn from
+    {4, 256, 65536} with 1/1/2-byte storage, uniform symbols, seed 0, built in
+    one persistent launch in the launch configuration the benchmark times;
+    every tree is compared with the oracle (serialWT, Fig. 1): bitmaps with
+    their padding, directories, zero counts and node table."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1407_8142_gb300 import autotune
+    serialwt.build_oracle()
+    specs4 = synth.config4_specs(4096, seed=0)
+    specs = [(n, sg, b) for n, sg, b, _ in specs4]
+    workers = max(2, min(16, os.cpu_count() or 2))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        host = list(ex.map(synth.config4_sequence, specs4))
+    seqs = [wt._torch_symbols(h) for h in host]
+    threads = autotune.tune_batch(specs, seqs)
+    with wt.Batch(specs, tile_threads=threads) as b:
+        b.set_inputs(seqs)
+        b.build()
+        assert b.sync() == 0
+        del seqs
+        torch.cuda.empty_cache()
+        # the oracle runs on host threads (its C code releases the GIL) while
+        # the main thread reads back and compares finished trees
+        with ThreadPoolExecutor(max_workers=workers) as ex:
+            window = 4 * workers
+            futs = {}
+            for i in range(min(window, len(host))):
+                futs[i] = ex.submit(serialwt.build, host[i], specs[i][1])
+            for i in range(len(host)):
+                ref = futs.pop(i).result()
+                j = i + window
+                if j < len(host):
+                    futs[j] = ex.submit(serialwt.build, host[j], specs[j][1])
+                compare_with_oracle(b.tree(i).to_host(), ref)
+                host[i] = None

@@ -1,15 +1,17 @@
 """Build server (continuous batching under an HBM budget).
 
-Every result built in the concurrent mix must be bit-identical to a
-standalone build of the same input; the budget must hold; requests that do
-not fit wait for memory instead of failing.
+Every result built in the concurrent mix must be bit-identical to the
+oracle's output for the same input (serialWT, Fig. 1); the budget must hold;
+requests that do not fit wait for memory instead of failing.
 """
 import time
 
 import numpy as np
 import pytest
 
+from oracle import serialwt
 from paper_1407_8142_gb300 import synth
+from tests._compare import compare_with_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -25,13 +27,11 @@ def wt():
     return mod
 
 
-def standalone(wt, S, sigma):
-    with wt.WaveletTree(S.size, sigma, S.dtype.itemsize) as t:
-        t.build(S)
-        return t.to_host()
+def check_with_oracle(got, S, sigma):
+    compare_with_oracle(got, serialwt.build(S, sigma))
 
 
-def test_results_equal_standalone_builds_in_the_mix(wt):
+def test_results_in_the_mix_match_oracle(wt):
     reqs = []
     k = 0
     for sigma, b in ((256, 1), (65536, 2), (1 << 20, 4), (5, 1)):
@@ -51,12 +51,7 @@ def test_results_equal_standalone_builds_in_the_mix(wt):
                 S, sg = reqs[ids[rid]]
                 view, status = srv.tree(rid)
                 assert status == 0
-                got = view.to_host()
-                want = standalone(wt, S, sg)
-                assert np.array_equal(got["bits"], want["bits"])
-                assert np.array_equal(got["rank"], want["rank"])
-                assert np.array_equal(got["zeros"], want["zeros"])
-                assert np.array_equal(got["node_start"], want["node_start"])
+                check_with_oracle(view.to_host(), S, sg)
                 srv.release(rid)
                 done[rid] = lat
 
@@ -107,3 +102,42 @@ def test_device_status_of_a_bad_request(wt):
         srv.poll()
         assert srv.tree(r_bad)[1] == wt.WT_ERR_SYMBOL
         assert srv.tree(r_good)[1] == 0
+
+
+def config5_sample(seed=0):
+    """A seeded sample of the serving workload's requests (Poisson arrivals
+    at 2000/s, n = floor(2^U(12, 24)), sigma in {256, 2^16, 2^20} with 1/2/4-byte
+    storage, Zipf(1.0) symbols): for every alphabet class its shortest and its
+    longest request of the 10 s trace and two drawn at random."""
+    reqs = synth.config5_requests(rate=2000.0, horizon_s=10.0, seed=seed)
+    pick = []
+    for sigma in (256, 1 << 16, 1 << 20):
+        idx = [i for i, r in enumerate(reqs) if r["sigma"] == sigma]
+        by_n = sorted(idx, key=lambda i: reqs[i]["n"])
+        x = synth.splitmix64_scalar(seed, 9000 + sigma)
+        pick += [by_n[0], by_n[-1], idx[x % len(idx)], idx[(x >> 32) % len(idx)]]
+    return [reqs[i] for i in sorted(set(pick))]
+
+
+def test_config5_sample_matches_oracle(wt):
+    """Requests of the serving workload, submitted back to back so that several
+    share a batch, each result compared with the oracle."""
+    from concurrent.futures import ThreadPoolExecutor
+    reqs = config5_sample()
+    assert {r["sigma"] for r in reqs} == {256, 1 << 16, 1 << 20}
+    assert max(r["n"] for r in reqs) > (1 << 23) and min(r["n"] for r in reqs) < (1 << 13)
+    payloads = [synth.config5_sequence(r) for r in reqs]
+    serialwt.build_oracle()
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        refs = [ex.submit(serialwt.build, S, r["sigma"]) for S, r in zip(payloads, reqs)]
+        with wt.Server(4 << 30, max_inflight=4) as srv:
+            ids = {srv.submit(S, r["sigma"]): k for k, (S, r) in enumerate(zip(payloads, reqs))}
+            assert srv.drain() == wt.WT_OK
+            got = srv.poll()
+            assert sorted(ids) == sorted(rid for rid, _ in got)
+            for rid, _ in got:
+                k = ids[rid]
+                view, status = srv.tree(rid)
+                assert status == 0
+                compare_with_oracle(view.to_host(), refs[k].result())
+                srv.release(rid)
