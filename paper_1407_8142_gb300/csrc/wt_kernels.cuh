@@ -654,10 +654,10 @@ __host__ __device__ constexpr uint32_t tab_smem_nodes() { return SB == 1 ? 128u 
 template <int SB, int THREADS, int DEPTH = 2, int WPT = 1>
 constexpr uint32_t split_smem_bytes() {
   // DEPTH input tiles, per-warp staging, per-word {bit word, warp-local
-  // ones-prefix}, per-warp {ones, prefix share}, the level table, mbarriers,
-  // tickets, run counters and run starts
+  // ones-prefix}, two sets (tile parity) of per-warp {ones, prefix share},
+  // the level table, mbarriers, tickets, run counters and run starts
   return DEPTH * 32u * WPT * THREADS * SB + (THREADS / 32) * stage_bytes<SB, WPT>() + 8u * WPT * THREADS +
-         8u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 192u;
+         16u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 192u;
 }
 
 // Phase C of a warp whose symbols span several nodes (the tile is not in
@@ -864,26 +864,107 @@ struct SplitShared {
   uint32_t *nc;    // node-count cache of thread 0: {node, ones of child 2 node, of child 2 node + 1}
 };
 
-// One tile of the split pass over level a.level: bits and directory of the
-// level, stable split into T_{level+1}, next-level ones per destination tile.
-// sIn holds the tile's symbols; share is this thread's part of the tile's
-// ones-prefix (summed over the block here).  Ends with a block barrier,
-// after which thread 0 has stored ring_value to *ring_slot (if non-null).
-// WPT: words (of 32 symbols) per thread; a warp's segment is 1024 * WPT
-// symbols (WPT > 1 only for 1-byte symbols).
+// Per-thread results of pass A that the rest of the tile uses.
+template <int WPT>
+struct SplitPassA {
+  uint32_t word[WPT];  // the thread's bitmap words
+  uint32_t pw[WPT];    // ones before each word, within the warp
+  uint32_t incl;       // ones through the thread's words, within the warp
+};
+
+// Pass A of a split tile: 32 * WPT consecutive symbols per thread -> WPT
+// bitmap words; warp scan of the ones; the thread's words and prefixes to
+// sWP, the warp's {ones, prefix share} to sWT.  The block barrier that makes
+// sWT complete is the caller's.
+template <int SB, int THREADS, int WPT>
+__device__ __forceinline__ SplitPassA<WPT> split_pass_a(const SplitArgs &a, const uint8_t *sIn, uint32_t nv,
+                                                        uint32_t share_part, uint2 *sWP, uint2 *sWT) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t k = a.L - 1 - a.level;
+  const uint32_t my0 = 32 * WPT * tid;
+  SplitPassA<WPT> r;
+  uint32_t pc = 0;
+#pragma unroll
+  for (int i = 0; i < WPT; ++i) {
+    r.word[i] = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k) & valid_mask(my0 + 32 * i, nv);
+    pc += __popc(r.word[i]);
+  }
+  uint32_t incl = pc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  r.incl = incl;
+  r.pw[0] = incl - pc;
+#pragma unroll
+  for (int i = 1; i < WPT; ++i) r.pw[i] = r.pw[i - 1] + __popc(r.word[i - 1]);
+#pragma unroll
+  for (int i = 0; i < WPT; ++i) sWP[WPT * tid + i] = make_uint2(r.word[i], r.pw[i]);
+  const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, share_part);
+  if (lane == 31) sWT[warp] = make_uint2(incl, share);
+  return r;
+}
+
+// The run counters of a finished single-node tile (node pf; 0xFFFFFFFF for
+// a tile over several nodes, whose counts went to global memory directly):
+// counters 0/1 belong to the zero run, 2/3 to the one run; threads 0..3 add
+// them to the next level's tile counts and clear them.  With node counts,
+// thread 0 also accumulates the node's ones (the zero run lies in child 2pf,
+// the one run in child 2pf+1; a node spans many tiles at shallow levels, so
+// the counts of the current node are kept in shared memory and flushed when
+// the node changes).
+template <bool NC>
+__device__ __forceinline__ void split_flush_runs(const SplitArgs &a, uint32_t *cnt, const uint32_t *run,
+                                                 uint32_t *nc, uint32_t pf) {
+  const uint32_t tid = threadIdx.x;
+  if (tid < 4 && pf != 0xFFFFFFFFu) {
+    const uint32_t v = cnt[tid];
+    if (NC && a.nones_next) {
+      const uint32_t pair = v + __shfl_down_sync(0xFu, v, 1);
+      const uint32_t p1 = __shfl_sync(0xFu, pair, 2);
+      if (tid == 0) {
+        if (nc[0] == pf) {
+          nc[1] += pair;
+          nc[2] += p1;
+        } else {
+          if (nc[0] != 0xFFFFFFFFu) {
+            if (nc[1]) atomicAdd(&a.nones_next[2 * nc[0]], nc[1]);
+            if (nc[2]) atomicAdd(&a.nones_next[2 * nc[0] + 1], nc[2]);
+          }
+          nc[0] = pf;
+          nc[1] = pair;
+          nc[2] = p1;
+        }
+      }
+    }
+    if (v) {
+      cnt[tid] = 0;
+      const uint32_t dt = (run[tid >> 1] >> a.log2T) + (tid & 1);
+      if (dt < a.NT) counts_add(a.cout, dt, v);
+    }
+  }
+}
+
+// The rest of a split tile after pass A and the block barrier behind it:
+// bits and directory of the level, stable split into T_{level+1}, next-level
+// ones per destination tile.  sIn holds the tile's symbols; pa is this
+// thread's pass-A result; sm.wt holds every warp's {ones, prefix share}.  A
+// single-node tile leaves its run counts in sm.cnt / sm.run for
+// split_flush_runs; the node of such a tile is returned (0xFFFFFFFF for a
+// tile over several nodes).  WPT: words (of 32 symbols) per thread; a warp's
+// segment is 1024 * WPT symbols (WPT > 1 only for 1-byte symbols).
 template <int SB, int THREADS, bool NC, int WPT = 1>
-__device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab, uint32_t tile,
-                                           const uint8_t *sIn, uint32_t share_part,
-                                           const SplitShared &sm, uint32_t *ring_slot,
-                                           uint32_t ring_value) {
+__device__ __forceinline__ uint32_t split_tile_rest(const SplitArgs &a, const uint2 *tab, uint32_t tile,
+                                                    const uint8_t *sIn, const SplitPassA<WPT> &pa,
+                                                    const SplitShared &sm) {
   static_assert(WPT == 1 || SB == 1, "several words per thread only for 1-byte symbols");
   using Sym = typename SymT<SB>::type;
   constexpr uint32_t T = 32 * WPT * THREADS;
   constexpr uint32_t SPW = 1024 * WPT;  // symbols per warp
   constexpr uint32_t NW = THREADS / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t k = a.L - 1 - a.level;   // bit of this level
-  const uint32_t k1 = k - 1;              // bit of the next level (k >= 1 here)
+  const uint32_t k1 = a.L - 2 - a.level;  // bit of the next level (this level reads bit k1 + 1)
   const uint32_t pshift = a.pshift;       // node prefix = symbol >> pshift
   const uint32_t lmask = (1u << a.L) - 1u;
   uint8_t *const stage = sm.stage + warp * stage_bytes<SB, WPT>();
@@ -894,44 +975,21 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
   uint32_t *const sRun = sm.run;
   const uint64_t start = (uint64_t)tile * T;
   const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+  const uint32_t my0 = 32 * WPT * tid;
+  const uint32_t incl = pa.incl;
 
-    // Pass A: 32 * WPT consecutive symbols per thread -> WPT bitmap words;
-    // warp scan of the ones.
-    const uint32_t my0 = 32 * WPT * tid;
-    uint32_t word[WPT];
-    uint32_t pc = 0;
-#pragma unroll
-    for (int i = 0; i < WPT; ++i) {
-      word[i] = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k) & valid_mask(my0 + 32 * i, nv);
-      pc += __popc(word[i]);
-    }
-    uint32_t incl = pc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= (uint32_t)o) incl += y;
-    }
-    uint32_t pw[WPT];  // ones before each word, within the warp
-    pw[0] = incl - pc;
-#pragma unroll
-    for (int i = 1; i < WPT; ++i) pw[i] = pw[i - 1] + __popc(word[i - 1]);
-#pragma unroll
-    for (int i = 0; i < WPT; ++i) sWP[WPT * tid + i] = make_uint2(word[i], pw[i]);
-    const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, share_part);
-    if (lane == 31) sWT[warp] = make_uint2(incl, share);
-    __syncthreads();
     const uint2 wv = lane < NW ? sWT[lane] : make_uint2(0, 0);
     const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);  // ones before the warp
     const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
     const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);                       // ones before the tile
     if (WPT == 1) {
-      write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, word[0], R, Pw + pw[0], total);
+      write_level<THREADS>(a.lo, tile, a.NT, start, my0, a.n, a.NB, a.W, pa.word[0], R, Pw + pa.pw[0], total);
     } else {
 #pragma unroll
       for (int i = 0; i < WPT; ++i) {
         const uint64_t widx = (uint64_t)tile * (WPT * THREADS) + WPT * tid + i;
-        if (widx < a.W) a.lo.bits[widx] = word[i];
-        if ((widx & 15) == 0 && start + my0 + 32 * i < a.n) a.lo.rank[(start + my0 + 32 * i) >> 9] = R + Pw + pw[i];
+        if (widx < a.W) a.lo.bits[widx] = pa.word[i];
+        if ((widx & 15) == 0 && start + my0 + 32 * i < a.n) a.lo.rank[(start + my0 + 32 * i) >> 9] = R + Pw + pa.pw[i];
       }
       if (tile == a.NT - 1 && tid == 0) {
         a.lo.rank[a.NB] = R + total;
@@ -986,7 +1044,7 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
         // one predicate, two predicated stores, two predicated increments --
         // no branch, whatever the bits.
         const uint32_t zbase = smem_addr(zS), obase = smem_addr(oS);
-#pragma unroll 2
+#pragma unroll
         for (uint32_t s = 0; s < 32 * WPT / G8; ++s) {
           const uint32_t pos0 = 32 * G8 * s + G8 * lane;
           const uint2 wp = sWP[32 * WPT * warp + G8 * s + wsub];
@@ -1080,40 +1138,25 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
                                  sWP + 32 * WPT * warp, seg, nvw, nzw, wpf, wpl, Zw, Ow, lmask, pshift, k1);
       }
     }
-    if (ring_slot) *ring_slot = ring_value;
-    __syncthreads();
-    if (tid < 4 && one_node) {
-      // single-node tile: counters 0/1 belong to the zero run, 2/3 to the one run
-      const uint32_t v = sm.cnt[tid];
-      if (NC && a.nones_next) {
-        // the zero run lies in child 2pf, the one run in child 2pf+1; a
-        // node spans many tiles at shallow levels, so thread 0 accumulates
-        // the current node's counts and flushes them when the node changes
-        const uint32_t pair = v + __shfl_down_sync(0xFu, v, 1);
-        const uint32_t p1 = __shfl_sync(0xFu, pair, 2);
-        if (tid == 0) {
-          // the tile's node, read again from the tile (still in shared memory)
-          const uint32_t pf = ((uint32_t)reinterpret_cast<const Sym *>(sIn)[0] & lmask) >> pshift;
-          if (sm.nc[0] == pf) {
-            sm.nc[1] += pair;
-            sm.nc[2] += p1;
-          } else {
-            if (sm.nc[0] != 0xFFFFFFFFu) {
-              if (sm.nc[1]) atomicAdd(&a.nones_next[2 * sm.nc[0]], sm.nc[1]);
-              if (sm.nc[2]) atomicAdd(&a.nones_next[2 * sm.nc[0] + 1], sm.nc[2]);
-            }
-            sm.nc[0] = pf;
-            sm.nc[1] = pair;
-            sm.nc[2] = p1;
-          }
-        }
-      }
-      if (v) {
-        sm.cnt[tid] = 0;
-        const uint32_t dt = (sm.run[tid >> 1] >> a.log2T) + (tid & 1);
-        if (dt < a.NT) counts_add(a.cout, dt, v);
-      }
-    }
+    return one_node ? pf : 0xFFFFFFFFu;
+}
+
+// One whole tile of the split pass (pass A, block barrier, the rest, block
+// barrier, run counts): for callers that process one tile at a time.  Ends
+// with thread 0 having stored ring_value to *ring_slot (if non-null).
+template <int SB, int THREADS, bool NC, int WPT = 1>
+__device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab, uint32_t tile,
+                                           const uint8_t *sIn, uint32_t share_part,
+                                           const SplitShared &sm, uint32_t *ring_slot,
+                                           uint32_t ring_value) {
+  constexpr uint32_t T = 32 * WPT * THREADS;
+  const uint32_t nv = (uint32_t)umin64(T, a.n - (uint64_t)tile * T);
+  const SplitPassA<WPT> pa = split_pass_a<SB, THREADS, WPT>(a, sIn, nv, share_part, sm.wp, sm.wt);
+  __syncthreads();
+  const uint32_t pf = split_tile_rest<SB, THREADS, NC, WPT>(a, tab, tile, sIn, pa, sm);
+  if (ring_slot) *ring_slot = ring_value;
+  __syncthreads();
+  split_flush_runs<NC>(a, sm.cnt, sm.run, sm.nc, pf);
 }
 
 // Resident CTAs per SM the split pass is compiled for: as many as shared
@@ -1143,13 +1186,13 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
   pipe.sIn1 = smem + (DEPTH - 1) * pipe.TB;
   uint8_t *const sStage = smem + DEPTH * pipe.TB;
   uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<SB, WPT>());  // {word, prefix}
-  uint2 *const sWT = sWP + WPT * THREADS;            // per warp {ones, prefix share}
-  uint2 *const sTab = sWT + NW;                      // level table (small levels)
+  uint2 *const sWT = sWP + WPT * THREADS;            // per warp {ones, prefix share}, 2 sets
+  uint2 *const sTab = sWT + 2 * NW;                  // level table (small levels)
   pipe.bar = reinterpret_cast<uint64_t *>(sTab + tab_smem_nodes<SB>());
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
-  uint32_t *const sCnt = pipe.ring + 4;              // 4 run counters
-  uint32_t *const sRun = sCnt + 4;                   // 2 run starts
-  uint32_t *const sNc = sRun + 2;                    // node-count cache (3 words)
+  uint32_t *const sCnt = pipe.ring + 4;              // 2 x 4 run counters
+  uint32_t *const sRun = sCnt + 8;                   // 2 x 2 run starts
+  uint32_t *const sNc = sRun + 4;                    // node-count cache (3 words)
   pipe.in = a.in;
   pipe.in_padded = a.in_padded;
   pipe.n = a.n;
@@ -1175,7 +1218,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
   } else if (tab_smem) {
     for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
   }
-  if (tid < 4) sCnt[tid] = 0;
+  if (tid < 8) sCnt[tid] = 0;
   if (tid == 0) {
     sNc[0] = 0xFFFFFFFFu;
     pipe.prologue();
@@ -1183,29 +1226,76 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
   __syncthreads();
   PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
 
-  for (uint32_t it = 0;; ++it) {
-    const uint32_t tile = pipe.ring[it % 3];
-    if (tile >= a.NT) break;
-    const uint32_t nxt = pipe.ring[(it + 1) % 3];
-    uint32_t nn = 0;
-    if (tid == 0) nn = pipe.advance(it, nxt);
-    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
-    const bool ok = pipe.wait(it, a.spin_limit, a.err);
-    if (__syncthreads_or(!ok)) {
-      pipe.drain(it, a.spin_limit, a.err);
-      __syncthreads();
-      break;
+  if constexpr (DEPTH == 2) {
+    // One block barrier per tile: the one that completes pass A.  What
+    // warps share across that barrier is kept per tile parity (the warps'
+    // pass-A sums, the run counters of single-node tiles), so that a warp
+    // may finish tile it while another has begun tile it+1; no warp gets
+    // further ahead, since the barrier of tile it+1 waits for all.  Behind
+    // that barrier every warp is done with tile it-1, so thread 0 then
+    // starts the copy of tile it+1 into that tile's buffer, and threads 0..3
+    // add the run counts of tile it-1 to the next level's tile counts.
+    uint32_t prev_pf = 0xFFFFFFFFu;  // node of the previous tile if it lay in one node
+    uint32_t it = 0;
+    for (;; ++it) {
+      const uint32_t tile = pipe.ring[it % 3];
+      if (tile >= a.NT) break;
+      const uint32_t nxt = pipe.ring[(it + 1) % 3];
+      uint32_t nn = 0;
+      if (tid == 0) nn = atomicAdd(a.ticket, 1u);  // the ticket of tile it+2
+      const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
+      const bool ok = pipe.wait(it, a.spin_limit, a.err);
+      const uint64_t start = (uint64_t)tile * T;
+      const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+      uint8_t *const sIn = pipe.data(it);
+      if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+      const uint32_t par = it & 1u;
+      const SplitShared sm{sStage, sWP, sWT + par * NW, sCnt + 4 * par, sRun + 2 * par, sNc};
+      const SplitPassA<WPT> pa = split_pass_a<SB, THREADS, WPT>(a, sIn, nv, pre.sum(), sWP, sm.wt);
+      if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
+      if (__syncthreads_or(!ok)) {
+        // the tile's copy did not land in time: wait once more (bounded)
+        // for it, the only copy in flight, and stop
+        if (tid == 0) mbar_wait_bounded(&pipe.bar[it & 1], (it >> 1) & 1u, a.spin_limit, a.err);
+        __syncthreads();
+        break;
+      }
+      if (tid == 0 && nxt < a.NT) {
+        fence_proxy_async_smem();
+        pipe.issue(nxt, (it + 1) & 1);
+      }
+      split_flush_runs<NC>(a, sCnt + 4 * (par ^ 1u), sRun + 2 * (par ^ 1u), sNc, prev_pf);
+      prev_pf = split_tile_rest<SB, THREADS, NC, WPT>(a, tab, tile, sIn, pa, sm);
+      pre = pre_next;
     }
-    const uint64_t start = (uint64_t)tile * T;
-    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
-    uint8_t *const sIn = pipe.data(it);
-    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+    __syncthreads();
+    const uint32_t lp = (it & 1u) ^ 1u;  // parity of the last tile processed
+    split_flush_runs<NC>(a, sCnt + 4 * lp, sRun + 2 * lp, sNc, prev_pf);
+  } else {
+    for (uint32_t it = 0;; ++it) {
+      const uint32_t tile = pipe.ring[it % 3];
+      if (tile >= a.NT) break;
+      const uint32_t nxt = pipe.ring[(it + 1) % 3];
+      uint32_t nn = 0;
+      if (tid == 0) nn = pipe.advance(it, nxt);
+      const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
+      const bool ok = pipe.wait(it, a.spin_limit, a.err);
+      if (__syncthreads_or(!ok)) {
+        pipe.drain(it, a.spin_limit, a.err);
+        __syncthreads();
+        break;
+      }
+      const uint64_t start = (uint64_t)tile * T;
+      const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+      uint8_t *const sIn = pipe.data(it);
+      if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
 
-    const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc};
-    split_tile<SB, THREADS, NC, WPT>(a, tab, tile, sIn, pre.sum(), sm, tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr,
-                                     nn);
-    if (DEPTH == 1 && tid == 0) pipe.after_tile(nxt);
-    pre = pre_next;
+      const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc};
+      split_tile<SB, THREADS, NC, WPT>(a, tab, tile, sIn, pre.sum(), sm,
+                                       tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
+      if (tid == 0) pipe.after_tile(nxt);
+      pre = pre_next;
+    }
   }
   if (NC && a.nones_next && tid == 0 && sNc[0] != 0xFFFFFFFFu) {  // the cached node's counts
     if (sNc[1]) atomicAdd(&a.nones_next[2 * sNc[0]], sNc[1]);
