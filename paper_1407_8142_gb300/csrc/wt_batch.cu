@@ -31,6 +31,9 @@ struct wt_batch {
   BTree *d_trees = nullptr;
   uint32_t *d_grp_first = nullptr;
   uint2 *d_grp = nullptr;
+  uint32_t *d_hint = nullptr;
+  uint32_t hint_shift = 5;
+  uint32_t max_sb = 1;               // widest symbol of the batch (sizes the kernel's tiles)
   uint32_t n_groups = 0, n_items = 0;
   unsigned char *d_mem = nullptr;    // outputs + scratch of every tree
   uint32_t *d_ctrl = nullptr;        // cleared per build: ticket, error, stamp, per-tree control blocks
@@ -52,6 +55,7 @@ int wt_batch_free(wt_batch *b) {
   cudaFree(b->d_trees);
   cudaFree(b->d_grp_first);
   cudaFree(b->d_grp);
+  cudaFree(b->d_hint);
   delete b;
   return WT_OK;
 }
@@ -81,6 +85,7 @@ int wt_batch_create(const wt_seq_desc *descs, uint32_t m, const wt_config *cfg, 
     }
     mem += batch_mem_bytes(geo[i]);
     ctrl += geo[i].ctrl;
+    b->max_sb = std::max(b->max_sb, descs[i].symbol_bytes);
   }
   auto fail = [&](cudaError_t err) {
     (void)cudaGetLastError();
@@ -128,6 +133,10 @@ int wt_batch_create(const wt_seq_desc *descs, uint32_t m, const wt_config *cfg, 
   std::vector<uint2> grp;
   b->n_items = batch_worklist(geo, first, grp);
   b->n_groups = (uint32_t)grp.size();
+  std::vector<uint32_t> hint;
+  b->hint_shift = batch_hints(first, b->n_items, 0xFFFFFFFFu, hint);
+  if ((e = cudaMalloc(&b->d_hint, hint.size() * 4))) return fail(e);
+  if ((e = cudaMemcpy(b->d_hint, hint.data(), hint.size() * 4, cudaMemcpyHostToDevice))) return fail(e);
   if ((e = cudaMalloc(&b->d_grp_first, first.size() * 4))) return fail(e);
   if ((e = cudaMalloc(&b->d_grp, grp.size() * sizeof(uint2)))) return fail(e);
   if ((e = cudaMalloc(&b->d_trees, m * sizeof(BTree)))) return fail(e);
@@ -162,13 +171,15 @@ int wt_batch_build(wt_batch *b, void *stream) {
   a.trees = b->d_trees;
   a.grp_first = b->d_grp_first;
   a.grp = b->d_grp;
+  a.hint = b->d_hint;
+  a.hint_shift = b->hint_shift;
   a.n_groups = b->n_groups;
   a.n_items = b->n_items;
   a.ticket = b->d_ctrl;
   a.spin_limit = b->cfg.spin_limit ? b->cfg.spin_limit : (1u << 22);
   a.err = reinterpret_cast<int *>(b->d_ctrl + 1);
   a.t_start = reinterpret_cast<unsigned long long *>(b->d_ctrl + 2);
-  WT_CUDA(batch_launch(a, b->threads, b->sms, b->cfg.ctas_per_sm, st));
+  WT_CUDA(batch_launch(a, b->threads, b->max_sb, b->sms, b->cfg.ctas_per_sm, st));
   return WT_OK;
 }
 

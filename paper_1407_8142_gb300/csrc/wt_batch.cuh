@@ -30,6 +30,8 @@ struct BatchArgs {
   const BTree *trees;
   const uint32_t *grp_first;  // n_groups + 1: first item of every group
   const uint2 *grp;           // n_groups: {tree, phase}
+  const uint32_t *hint;       // group of item i << hint_shift, for every such item
+  uint32_t hint_shift;
   uint32_t n_groups, n_items;
   uint32_t *ticket;
   uint32_t spin_limit;
@@ -62,26 +64,54 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-template <int THREADS>
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// The symbols an item of `phase` reads: S for the pre-pass, for level 0 and
+// for the only level of a one-level tree; else the ping-pong buffer the
+// previous level wrote (whole tiles).
+__device__ __forceinline__ const uint8_t *item_input(const BTree &tr, uint32_t phase) {
+  const uint32_t level = phase >= 2 ? phase - 2 : 0;
+  if (phase == 0 || level == 0 || tr.L < 2) return tr.in;
+  return tr.buf[(level - 1) & 1];
+}
+
+// Input tiles in flight per block: three, or two when the batch holds
+// 4-byte symbols (their tiles are large).
+template <int MAXSB>
+__host__ __device__ constexpr uint32_t batch_slots() { return MAXSB == 4 ? 2u : 3u; }
+
+// One work item as the producer warp hands it to the consumer warps.
+struct BatchSlot {
+  BTree tr;            // the item's tree
+  uint32_t phase, tile, flags;
+  uint32_t prefix;     // ones of the item's level before its tile (split and last-level items)
+};
+constexpr uint32_t kSlotEnd = 1;   // no more items
+constexpr uint32_t kSlotSkip = 2;  // the item's dependency wait ran out: skip its work
+
+template <int THREADS, int MAXSB>
 constexpr uint32_t batch_smem_bytes() {
-  // one input tile of up to 4-byte symbols, per-warp staging (also the
-  // shared histogram of the pre-pass), {word, prefix} per thread, per-warp
-  // {ones, share}, mbarrier and scratch words
-  return 32u * THREADS * 4 + (THREADS / 32) * stage_bytes<4>() + 8u * THREADS + 8u * (THREADS / 32) +
-         64u;
+  // the ring of input tiles (symbols of up to MAXSB bytes), per-warp staging
+  // (also the shared histogram of the pre-pass), {word, prefix} per thread,
+  // per-warp {ones, share}, slot descriptors, full and empty mbarriers,
+  // split-run counters and the table scan's warp sums
+  return batch_slots<MAXSB>() * 32u * THREADS * MAXSB + (THREADS / 32) * stage_bytes<MAXSB>() + 8u * THREADS +
+         8u * (THREADS / 32) + batch_slots<MAXSB>() * (uint32_t)sizeof(BatchSlot) + 16u * batch_slots<MAXSB>() +
+         32u + 4u * 33u + 16u;
 }
 
 constexpr uint32_t kBatchHistSmem = 8192;  // histograms up to this many bins in shared memory
 
-template <int SB, int THREADS>
-__device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8_t *sIn,
+// The work of one item (a tile of the pre-pass, of a split level or of the
+// last level) by the consumer warps; sIn holds the tile's symbols.
+template <int SB, int THREADS, int MAXSB>
+__device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint32_t share_part, uint8_t *sIn,
                            uint8_t *sStage, uint2 *sWP, uint2 *sWT, uint32_t *sMisc,
                            uint32_t spin_limit) {
-  constexpr uint32_t T = 32 * THREADS;
   const uint32_t tid = threadIdx.x;
   const uint32_t L = tr.L;
-  const uint64_t start = (uint64_t)tile * T;
-  const uint32_t nv = (uint32_t)umin64(T, tr.n - start);
   if (phase == 0) {
     PrepassArgs a;
     a.in = tr.in;
@@ -98,9 +128,12 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     uint32_t bad = 0;
     const uint32_t nbins = 1u << L;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(sStage);
-    if (nbins <= kBatchHistSmem && nbins * 4 <= (THREADS / 32) * stage_bytes<4>()) {
+    if (nbins <= kHistBallotMaxBins) {
+      // few bins: shared-memory atomics of a row would collide on them
+      prepass_tile<SB, THREADS, kHistBallot>(a, tile, sIn, nullptr, sMisc, bad, nullptr, 0);
+    } else if (nbins <= kBatchHistSmem && nbins * 4 <= (THREADS / 32) * stage_bytes<MAXSB>()) {
       for (uint32_t i = tid; i < nbins; i += THREADS) s_hist[i] = 0;
-      __syncthreads();
+      cta_sync<THREADS>();
       prepass_tile<SB, THREADS, kHistSmem>(a, tile, sIn, s_hist, sMisc, bad, nullptr, 0);
       for (uint32_t i = tid; i < nbins; i += THREADS)
         if (s_hist[i]) atomicAdd(&tr.hist[i], s_hist[i]);
@@ -111,10 +144,8 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     return;
   }
   const uint32_t level = phase - 2;  // split level, or L-1 for the last level
-  const PrefixLoads pre = prefix_loads<THREADS>(tree_counts(tr, level), tile, tr.NT);
   const LevelOut lo{tr.bits + (uint64_t)level * tr.W, tr.rank + (uint64_t)level * (tr.NB + 1),
                     tr.zeros + level};
-  (void)nv;
   if (level + 1 < L) {
     SplitArgs a;
     a.in = level == 0 ? tr.in : tr.buf[(level - 1) & 1];
@@ -138,10 +169,10 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     a.ticket = nullptr;
     a.spin_limit = spin_limit;
     a.err = tr.err;
-    const SplitShared sm{sStage, sWP, sWT, sMisc, sMisc + 4};
+    const SplitShared sm{sStage, sWP, sWT, sMisc, sMisc + 4, nullptr};
     if (tid < 4) sMisc[tid] = 0;
-    __syncthreads();
-    split_tile<SB, THREADS, false>(a, a.tab, tile, sIn, pre.sum(), sm, nullptr, 0);
+    cta_sync<THREADS>();
+    split_tile<SB, THREADS, false>(a, a.tab, tile, sIn, share_part, sm, nullptr, 0);
   } else {
     LeafArgs a;
     a.in = L >= 2 ? tr.buf[(L - 2) & 1] : tr.in;
@@ -156,112 +187,281 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint8
     a.ticket = nullptr;
     a.spin_limit = spin_limit;
     a.err = tr.err;
-    leaf_tile<SB, THREADS>(a, tile, sIn, pre.sum(), sWT, nullptr, 0);
+    leaf_tile<SB, THREADS>(a, tile, sIn, share_part, sWT, nullptr, 0);
   }
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_batch(BatchArgs a) {
+// Items a producer takes per ticket: consecutive items mostly share a group
+// (tree and phase), so one group search, one descriptor and one dependency
+// wait serve several items.
+constexpr uint32_t kBatchChunk = 4;
+
+// Publish the completion of the item a slot held (one thread of the
+// producer warp, after the consumers released the slot): the consumers'
+// writes, ordered before their release of the slot, become visible to the
+// whole GPU before the tree's phase counter that later phases wait for.
+__device__ __forceinline__ void batch_publish(const BatchSlot &sl) {
+  __threadfence();
+  const uint32_t prev = atomicAdd(&sl.tr.done[sl.phase], 1u);
+  if (sl.phase + 1 == sl.tr.phases && prev + 1 == phase_items(sl.tr, sl.phase)) *sl.tr.t_done = global_timer();
+}
+
+// The producer warp: takes kBatchChunk consecutive items per ticket, finds
+// each item's group (a hint per 2^hint_shift items, then a warp-wide search
+// of the next 32 group starts; consecutive items of one group reuse it),
+// copies the tree's descriptor into the next free slot, waits (bounded)
+// until the tree's previous phase is complete, sums the item's count prefix,
+// and starts the tile's copy into the slot's buffer (TMA), whose completion
+// the slot's full barrier counts.  It runs up to batch_slots() items ahead
+// of the consumers, and it publishes every item's completion as soon as the
+// consumers release its slot -- also while it waits for a dependency, so
+// that no completion it holds can hold up another block.
+template <int THREADS, int MAXSB>
+__device__ __forceinline__ void batch_producer(const BatchArgs &a, uint8_t *sBuf, BatchSlot *sSlot,
+                                               uint64_t *full, uint64_t *empty) {
+  constexpr uint32_t T = 32 * THREADS;
+  constexpr uint32_t TB = T * MAXSB;
+  constexpr uint32_t R = batch_slots<MAXSB>();
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t item = 0, left = 0;               // the current chunk
+  uint32_t next_chunk = 0;                   // lane 0: the ticket of the chunk after it (fetched early)
+  if (lane == 0) next_chunk = atomicAdd(a.ticket, kBatchChunk);
+  uint32_t g = 0, g_lo = 1, g_hi = 0;        // the current group and its items [g_lo, g_hi)
+  uint32_t ready = 0xFFFFFFFFu;              // group whose dependency was seen complete
+  // the previous split or last-level item: its group, tile, prefix and own count
+  uint32_t pv_g = 0xFFFFFFFFu, pv_tile = 0, pv_prefix = 0, pv_c0 = 0;
+  // lane 0: uses of each slot handed to the consumers and not yet published
+  // (bit s), and the use index of each
+  uint32_t pending = 0, use_of[R];
+#pragma unroll
+  for (uint32_t i = 0; i < R; ++i) use_of[i] = 0;
+  // lane 0: publish every pending slot the consumers have released
+  auto publish_released = [&]() {
+#pragma unroll
+    for (uint32_t i = 0; i < R; ++i)
+      if ((pending >> i) & 1u)
+        if (mbar_try_wait(&empty[i], (use_of[i] / R) & 1u)) {
+          batch_publish(sSlot[i]);
+          pending &= ~(1u << i);
+        }
+  };
+  bool alive = true;
+  for (uint32_t u = 0;; ++u) {
+    const uint32_t s = u % R;
+    if (u >= R) {
+      // the consumers release slot s after its previous item; publish it
+      uint32_t ok = 1;
+      if (lane == 0 && ((pending >> s) & 1u)) {
+        ok = mbar_wait_bounded(&empty[s], (use_of[s] / R) & 1u, a.spin_limit, a.err);
+        if (ok) {
+          batch_publish(sSlot[s]);
+          pending &= ~(1u << s);
+        }
+      }
+      if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) {
+        alive = false;  // the consumers stop on their own bounded wait
+        break;
+      }
+    }
+    if (left == 0) {
+      uint32_t t = 0;
+      if (lane == 0) {
+        t = next_chunk;
+        if (t < a.n_items) next_chunk = atomicAdd(a.ticket, kBatchChunk);
+      }
+      item = __shfl_sync(0xFFFFFFFFu, t, 0);
+      left = kBatchChunk;
+    } else {
+      ++item;
+    }
+    --left;
+    if (item >= a.n_items) {
+      if (lane == 0) {
+        sSlot[s].flags = kSlotEnd;
+        mbar_arrive(&full[s]);
+      }
+      break;
+    }
+    if (item == 0 && lane == 0) *a.t_start = global_timer();
+    if (item < g_lo || item >= g_hi) {
+      g = (item >= g_hi && item < g_hi + 32) ? g : __ldg(&a.hint[item >> a.hint_shift]);
+      for (;;) {
+        const uint32_t c = g + 1 + lane;
+        const bool le = c < a.n_groups && __ldg(&a.grp_first[c]) <= item;  // group starts rise
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, le);
+        g += __popc(bal);
+        if (bal != 0xFFFFFFFFu) break;
+      }
+      g_lo = __ldg(&a.grp_first[g]);
+      g_hi = __ldg(&a.grp_first[g + 1]);
+    }
+    const uint2 gp = __ldg(&a.grp[g]);
+    const uint32_t phase = gp.y;
+    const uint32_t tile = item - g_lo;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(a.trees + gp.x);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sSlot[s].tr);
+    for (uint32_t w = lane; w < (uint32_t)(sizeof(BTree) / 4); w += 32) dst[w] = __ldg(src + w);
+    __syncwarp();
+    const BTree &tr = sSlot[s].tr;
+    uint32_t flags = 0, fresh = 0;
+    if (lane == 0 && phase > 0 && ready != g) {
+      const uint32_t want = phase_items(tr, phase - 1);
+      uint32_t spins = 0;
+      while (ld_acquire(&tr.done[phase - 1]) < want) {
+        publish_released();
+        if (++spins > a.spin_limit) {
+          flags = kSlotSkip;
+          latch_error(a.err, WT_ERR_TIMEOUT);
+          latch_error(tr.err, WT_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(spins < 64 ? 64 : 512);
+      }
+      if (!flags) {
+        ready = g;
+        fresh = 1;
+      }
+    }
+    ready = __shfl_sync(0xFFFFFFFFu, ready, 0);
+    flags = __shfl_sync(0xFFFFFFFFu, flags, 0);
+    __syncwarp();  // the dependency seen complete before the count loads
+    uint32_t prefix = 0;
+    if (phase >= 2 && !flags) {
+      // the tile's exclusive ones-prefix from the level's tile counts: the
+      // previous tile's prefix plus its count when this item follows it,
+      // else a sum of up to (tile >> 12) + 126 terms; the tile's own count
+      // is loaded for the next item
+      const TileCounts c = tree_counts(tr, phase - 2);
+      if (g == pv_g && tile == pv_tile + 1) {
+        prefix = pv_prefix + pv_c0;
+      } else {
+        const uint32_t nt = prefix_terms(tile);
+        for (uint32_t j = lane; j < nt; j += 32) prefix += __ldcg(prefix_term(c, tile, j));
+        prefix = __reduce_add_sync(0xFFFFFFFFu, prefix);
+      }
+      pv_g = g;
+      pv_tile = tile;
+      pv_prefix = prefix;
+      pv_c0 = tile + 1 < tr.NT ? __ldcg(&c.c0[tile]) : 0u;
+    }
+    if (lane == 0) {
+      sSlot[s].phase = phase;
+      sSlot[s].tile = tile;
+      sSlot[s].flags = flags;
+      sSlot[s].prefix = prefix;
+      if (phase != 1 && flags == 0) {
+        const uint8_t *in = item_input(tr, phase);
+        const uint64_t start = (uint64_t)tile * T;
+        const uint32_t nv = (uint32_t)umin64(T, tr.n - start);
+        const uint32_t bytes = in != tr.in ? T * tr.sb : ((nv * tr.sb) & ~15u);
+        // the previous phase's generic writes (seen complete just now)
+        // before the async-proxy read of the copy
+        if (fresh) fence_proxy_async_global();
+        mbar_arrive_expect_tx(&full[s], bytes);
+        if (bytes) bulk_g2s(sBuf + s * TB, in + start * tr.sb, bytes, &full[s]);
+      } else {
+        mbar_arrive(&full[s]);
+      }
+      pending |= 1u << s;
+      use_of[s] = u;
+    }
+    __syncwarp();
+  }
+  // publish what the consumers still finish
+  if (lane == 0 && alive) {
+#pragma unroll
+    for (uint32_t i = 0; i < R; ++i)
+      if ((pending >> i) & 1u) {
+        if (!mbar_wait_bounded(&empty[i], (use_of[i] / R) & 1u, a.spin_limit, a.err)) break;
+        batch_publish(sSlot[i]);
+      }
+  }
+}
+
+// Batched build: THREADS consumer threads and one producer warp per block.
+// Consumers take the slots in order: wait for the slot's item (bounded), do
+// its work, and, behind a barrier of the consumer warps, release the slot to
+// the producer (which then publishes the item's completion).
+// Resident blocks per SM the batched kernel is compiled for (its shared
+// memory allows as many; registers are capped to match).
+template <int THREADS, int MAXSB>
+constexpr int batch_min_blocks() {
+  return MAXSB == 4 ? (THREADS == 128 ? 4 : 2) : (THREADS == 128 ? 6 : 3);
+}
+
+template <int THREADS, int MAXSB>
+__global__ void __launch_bounds__(THREADS + 32, batch_min_blocks<THREADS, MAXSB>()) k_batch(BatchArgs a) {
   constexpr uint32_t T = 32 * THREADS;
   constexpr uint32_t NW = THREADS / 32;
+  constexpr uint32_t TB = T * MAXSB;
+  constexpr uint32_t R = batch_slots<MAXSB>();
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *const sIn = smem;
-  uint8_t *const sStage = smem + T * 4;
-  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<4>());
+  uint8_t *const sBuf = smem;
+  uint8_t *const sStage = smem + R * TB;
+  uint2 *const sWP = reinterpret_cast<uint2 *>(sStage + NW * stage_bytes<MAXSB>());
   uint2 *const sWT = sWP + THREADS;
-  uint64_t *const bar = reinterpret_cast<uint64_t *>(sWT + NW);
-  uint32_t *const sMisc = reinterpret_cast<uint32_t *>(bar + 1);  // item, and split counters
-  __shared__ uint32_t s_item, s_ok;
-  __shared__ uint32_t s_warp[33];
+  BatchSlot *const sSlot = reinterpret_cast<BatchSlot *>(sWT + NW);
+  uint64_t *const full = reinterpret_cast<uint64_t *>(sSlot + R);
+  uint64_t *const empty = full + R;
+  uint32_t *const sMisc = reinterpret_cast<uint32_t *>(empty + R);  // split-run counters and starts
+  uint32_t *const s_warp = sMisc + 8;                               // 33 words
   const uint32_t tid = threadIdx.x;
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (uint32_t i = 0; i < R; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t parity = 0;
-
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(a.ticket, 1u);
-    __syncthreads();
-    const uint32_t item = s_item;
-    if (item >= a.n_items) break;
-    if (item == 0 && tid == 0) *a.t_start = global_timer();
-    // group of this item: last g with grp_first[g] <= item
-    uint32_t lo = 0, hi = a.n_groups - 1;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi + 1) >> 1;
-      if (a.grp_first[mid] <= item) lo = mid;
-      else hi = mid - 1;
+  if (tid >= THREADS) {
+    batch_producer<THREADS, MAXSB>(a, sBuf, sSlot, full, empty);
+    return;
+  }
+  for (uint32_t u = 0;; ++u) {
+    const uint32_t s = u % R;
+    const bool ok = mbar_wait_bounded(&full[s], (u / R) & 1u, a.spin_limit, a.err);
+    if (cta_sync_or<THREADS>(!ok)) {
+      // the slot's item or its copy did not arrive in time: wait once more
+      // (bounded) for a copy that may still be in flight, and stop
+      if (tid == 0) mbar_wait_bounded(&full[s], (u / R) & 1u, a.spin_limit, a.err);
+      cta_sync<THREADS>();
+      return;
     }
-    const uint2 gp = a.grp[lo];
-    const uint32_t phase = gp.y;
-    const uint32_t tile = item - a.grp_first[lo];
-    const BTree tr = a.trees[gp.x];
-    // wait for the tree's previous phase (bounded)
-    if (tid == 0) {
-      uint32_t ok = 1;
-      if (phase > 0) {
-        const uint32_t want = phase_items(tr, phase - 1);
-        uint32_t spins = 0;
-        while (ld_acquire(&tr.done[phase - 1]) < want) {
-          if (++spins > a.spin_limit) {
-            ok = 0;
-            latch_error(a.err, WT_ERR_TIMEOUT);
-            latch_error(tr.err, WT_ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(spins < 64 ? 64 : 512);
-        }
-      }
-      s_ok = ok;
-    }
-    __syncthreads();
-    if (s_ok) {
+    const BatchSlot &sl = sSlot[s];
+    if (sl.flags & kSlotEnd) return;
+    const BTree &tr = sl.tr;
+    const uint32_t phase = sl.phase, tile = sl.tile;
+    if (!(sl.flags & kSlotSkip)) {
       if (phase == 1) {
         tables_one_cta<THREADS>(tr.hist, tr.L, tr.node_start, tr.tab, s_warp);
       } else {
-        // the tile's symbols into shared memory (TMA), tail bytes by hand
-        const uint32_t level = phase >= 2 ? phase - 2 : 0;
-        const uint8_t *in = phase == 0 ? tr.in
-                            : (level == 0 || (level + 1 == tr.L && tr.L < 2)) ? tr.in
-                                                                              : tr.buf[(level - 1) & 1];
-        const bool padded = in != tr.in;
+        uint8_t *const sIn = sBuf + s * TB;
+        const uint8_t *in = item_input(tr, phase);
         const uint64_t start = (uint64_t)tile * T;
         const uint32_t nv = (uint32_t)umin64(T, tr.n - start);
-        const uint32_t bytes = padded ? T * tr.sb : ((nv * tr.sb) & ~15u);
-        if (tid == 0) {
-          fence_proxy_async_global();
-          mbar_arrive_expect_tx(bar, bytes);
-          if (bytes) bulk_g2s(sIn, in + start * tr.sb, bytes, bar);
-        }
-        const bool ok = mbar_wait_bounded(bar, parity, a.spin_limit, tr.err);
-        parity ^= 1u;
-        if (__syncthreads_or(!ok)) {
-          // the copy did not land in time: wait once more (bounded) and stop
-          if (tid == 0) mbar_wait_bounded(bar, parity ^ 1u, a.spin_limit, tr.err);
-          __syncthreads();
-          return;
-        }
-        if (!padded && ((nv * tr.sb) & 15u)) {
+        if (in == tr.in && ((nv * tr.sb) & 15u)) {  // tail bytes the bulk copy left out
           for (uint32_t i = ((nv * tr.sb) & ~15u) + tid; i < nv * tr.sb; i += THREADS)
             sIn[i] = in[start * tr.sb + i];
-          __syncthreads();
+          cta_sync<THREADS>();
         }
+        const uint32_t share = tid == 0 ? sl.prefix : 0u;
         switch (tr.sb) {
-          case 1: batch_tile<1, THREADS>(tr, phase, tile, sIn, sStage, sWP, sWT, sMisc, a.spin_limit); break;
-          case 2: batch_tile<2, THREADS>(tr, phase, tile, sIn, sStage, sWP, sWT, sMisc, a.spin_limit); break;
-          default: batch_tile<4, THREADS>(tr, phase, tile, sIn, sStage, sWP, sWT, sMisc, a.spin_limit); break;
+          case 1: batch_tile<1, THREADS, MAXSB>(tr, phase, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit); break;
+          case 2:
+            if constexpr (MAXSB >= 2)
+              batch_tile<2, THREADS, MAXSB>(tr, phase, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit);
+            break;
+          default:
+            if constexpr (MAXSB >= 4)
+              batch_tile<4, THREADS, MAXSB>(tr, phase, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit);
+            break;
         }
       }
     }
-    // publish the item's completion
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      const uint32_t prev = atomicAdd(&tr.done[phase], 1u);
-      if (phase + 1 == tr.phases && prev + 1 == phase_items(tr, phase)) *tr.t_done = global_timer();
-    }
+    // release the slot; the producer publishes the item's completion
+    cta_sync<THREADS>();
+    if (tid == 0) mbar_arrive(&empty[s]);
   }
 }
 
@@ -374,25 +574,51 @@ inline uint32_t batch_worklist(const std::vector<BatchGeo> &geo, std::vector<uin
   return items;
 }
 
-// Launch the batch kernel over a work list on `stream`.
-inline cudaError_t batch_launch(const BatchArgs &a, uint32_t threads, int sms, uint32_t ctas_per_sm,
-                                cudaStream_t st) {
+// Hints for the producer's group search: hint[h] = the group of item
+// h << shift.  shift >= 5, and larger when the table would exceed max_hints
+// entries (the search then walks several windows of 32 groups per item).
+inline uint32_t batch_hints(const std::vector<uint32_t> &first, uint32_t items, uint32_t max_hints,
+                            std::vector<uint32_t> &hint) {
+  uint32_t shift = 5;
+  while (((uint64_t)items >> shift) + 1 > max_hints) ++shift;
+  const uint32_t nh = (items >> shift) + 1;
+  hint.assign(nh, 0);
+  uint32_t g = 0;
+  const uint32_t ng = (uint32_t)first.size() - 1;
+  for (uint32_t h = 0; h < nh; ++h) {
+    const uint64_t item = (uint64_t)h << shift;
+    while (g + 1 < ng && first[g + 1] <= item) ++g;
+    hint[h] = g;
+  }
+  return shift;
+}
+
+// Launch the batch kernel over a work list on `stream`: blocks of `threads`
+// consumer threads plus a producer warp, tiles sized for max_sb-byte symbols.
+inline cudaError_t batch_launch(const BatchArgs &a, uint32_t threads, uint32_t max_sb, int sms,
+                                uint32_t ctas_per_sm, cudaStream_t st) {
   auto go = [&](auto kern, uint32_t th, size_t sm) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, th, sm) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, th + 32, sm) != cudaSuccess) {
       (void)cudaGetLastError();
       occ = 1;
     }
     occ = std::max(occ, 1);
     if (ctas_per_sm) occ = std::min<int>(occ, (int)ctas_per_sm);
     const int grid = (int)std::min<uint64_t>((uint64_t)occ * sms, std::max<uint32_t>(a.n_items, 1));
-    kern<<<grid, th, sm, st>>>(a);
+    kern<<<grid, th + 32, sm, st>>>(a);
     return cudaGetLastError();
   };
-  if (threads == 128) return go(k_batch<128>, 128, batch_smem_bytes<128>());
-  return go(k_batch<256>, 256, batch_smem_bytes<256>());
+  if (threads == 128) {
+    if (max_sb <= 1) return go(k_batch<128, 1>, 128, batch_smem_bytes<128, 1>());
+    if (max_sb <= 2) return go(k_batch<128, 2>, 128, batch_smem_bytes<128, 2>());
+    return go(k_batch<128, 4>, 128, batch_smem_bytes<128, 4>());
+  }
+  if (max_sb <= 1) return go(k_batch<256, 1>, 256, batch_smem_bytes<256, 1>());
+  if (max_sb <= 2) return go(k_batch<256, 2>, 256, batch_smem_bytes<256, 2>());
+  return go(k_batch<256, 4>, 256, batch_smem_bytes<256, 4>());
 }
 
 }  // namespace

@@ -146,9 +146,32 @@ static __device__ __noinline__ uint32_t lookback(const Lookback &lb, uint32_t ti
   return lookback_inline(lb, tile, first, aggregate);
 }
 
+// Barrier over the first THREADS threads of the block (named barrier 1,
+// with the memory ordering of a block barrier).  In a kernel whose blocks
+// have exactly THREADS threads it is a block barrier; the batched build's
+// consumer warps use it without the block's producer warp.
+template <int THREADS>
+__device__ __forceinline__ void cta_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(THREADS) : "memory");
+}
+
+// The same barrier, returning whether p held in any of the THREADS threads.
+template <int THREADS>
+__device__ __forceinline__ bool cta_sync_or(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, s;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred s, 1, %2, q;\n\tselp.u32 %0, 1, 0, s;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)p), "n"(THREADS)
+      : "memory");
+  return r != 0;
+}
+
 // Block-wide exclusive scan of one uint32 per thread.  s_warp holds >= 33
 // words.  Returns the thread's exclusive prefix; *total gets the block sum.
-// Contains two __syncthreads; callers must sync before reusing s_warp.
+// Contains two barriers over the THREADS threads (cta_sync); callers must
+// sync before reusing s_warp.
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp,
                                                          uint32_t *total) {
@@ -161,7 +184,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     if (lane >= (uint32_t)o) x += y;
   }
   if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
+  cta_sync<THREADS>();
   if (warp == 0) {
     uint32_t w = lane < (uint32_t)NW ? s_warp[lane] : 0u;
 #pragma unroll
@@ -171,7 +194,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     }
     s_warp[lane] = w;  // inclusive over warps
   }
-  __syncthreads();
+  cta_sync<THREADS>();
   *total = s_warp[NW - 1];
   return (warp ? s_warp[warp - 1] : 0u) + x - v;
 }
@@ -192,7 +215,7 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan64(unsigned lo
     if (lane >= (uint32_t)o) x += y;
   }
   if (lane == 31) s_warp[warp] = x;
-  __syncthreads();
+  cta_sync<THREADS>();
   if (warp == 0) {
     unsigned long long w = lane < (uint32_t)NW ? s_warp[lane] : 0ull;
 #pragma unroll
@@ -202,7 +225,7 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan64(unsigned lo
     }
     s_warp[lane] = w;
   }
-  __syncthreads();
+  cta_sync<THREADS>();
   *total = s_warp[NW - 1];
   return (warp ? s_warp[warp - 1] : 0ull) + x - v;
 }

@@ -240,7 +240,13 @@ constexpr uint32_t pipe_smem_bytes() {
 // every bin per lane: bin v of lane i at v * 32 + i, so the 32 updates of a
 // warp row always fall in 32 distinct banks (the copies are summed once per
 // CTA, each thread reading its bin's copies in a rotated order).
-enum HistMode : int { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2, kHistLanes = 3 };
+// One more for tiles handled one at a time (the batched build), where no
+// per-CTA histogram outlives the tile: kHistBallot (up to 16 bins) counts
+// each row with one ballot per bin and adds every warp's counts to the
+// global bins at the end of the tile (shared-memory atomics of a row would
+// collide on so few bins).
+enum HistMode : int { kHistNone = 0, kHistSmem = 1, kHistGlobal = 2, kHistLanes = 3, kHistBallot = 4 };
+constexpr uint32_t kHistBallotMaxBins = 16;
 constexpr uint32_t kHistLanesMaxBins = 256;
 constexpr uint32_t kHotSlots = 1024;  // per-CTA table of hot bins for kHistGlobal
 constexpr uint32_t kHotEmpty = 0xFFFFFFFFu;
@@ -313,6 +319,7 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
   const Sym *rows = reinterpret_cast<const Sym *>(sIn) + 1024 * warp;
   const uint32_t seg = 1024 * warp;
   const uint32_t nvw = nv > seg ? min(nv - seg, 1024u) : 0u;  // warp-uniform
+  uint32_t bcnt = 0;  // kHistBallot: lane b's count of bin b in the warp's rows
   if (HIST == kHistNone) {
     // range check only, and only when the storage type can exceed sigma
     if (a.sigma < (SB == 4 ? 0xFFFFFFFFu : (1u << (8 * SB)))) {
@@ -332,6 +339,11 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
         atomicAdd(&s_hist[v * 32 + lane], 1u);
       } else if (HIST == kHistSmem) {
         atomicAdd(&s_hist[v], 1u);
+      } else if (HIST == kHistBallot) {
+        for (uint32_t b = 0; b < (1u << a.L); ++b) {
+          const uint32_t c = __popc(__ballot_sync(0xFFFFFFFFu, v == b));
+          bcnt += lane == b ? c : 0u;
+        }
       } else {
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, v);
         if (lane == (uint32_t)(__ffs(peers) - 1)) hist_add(a.hist, s_hist, v, (uint32_t)__popc(peers));
@@ -347,6 +359,11 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
         if (valid) atomicAdd(&s_hist[v * 32 + lane], 1u);
       } else if (HIST == kHistSmem) {
         if (valid) atomicAdd(&s_hist[v], 1u);
+      } else if (HIST == kHistBallot) {
+        for (uint32_t b = 0; b < (1u << a.L); ++b) {
+          const uint32_t c = __popc(__ballot_sync(0xFFFFFFFFu, valid && v == b));
+          bcnt += lane == b ? c : 0u;
+        }
       } else {
         const uint32_t am = __ballot_sync(0xFFFFFFFFu, valid);
         if (valid) {
@@ -356,9 +373,10 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
       }
     }
   }
+  if (HIST == kHistBallot && bcnt) atomicAdd(&a.hist[lane], bcnt);
   const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, __popc(word));
   if (lane == 0) s_wt[warp] = wsum;
-  __syncthreads();
+  cta_sync<THREADS>();
   if (warp == 0 && a.L) {
     const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, lane < NW ? s_wt[lane] : 0u);
     if (lane == 0) {
@@ -370,7 +388,7 @@ __device__ __forceinline__ void prepass_tile(const PrepassArgs &a, uint32_t tile
     }
   }
   if (ring_slot) *ring_slot = ring_value;
-  __syncthreads();
+  cta_sync<THREADS>();
 }
 
 // Reads S once: the 2^L-bin histogram (node sizes of every level; not for
@@ -480,14 +498,14 @@ __device__ __forceinline__ void leaf_tile(const LeafArgs &a, uint32_t tile, cons
   }
   const uint32_t share = __reduce_add_sync(0xFFFFFFFFu, share_part);
   if (lane == 31) s_wt[warp] = make_uint2(incl, share);
-  __syncthreads();
+  cta_sync<THREADS>();
   const uint2 wv = lane < NW ? s_wt[lane] : make_uint2(0, 0);
   const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);
   const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
   const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);
   write_level<THREADS>(a.out, tile, a.NT, start, my0, a.n, a.NB, a.W, word, R, Pw + incl - pc, total);
   if (ring_slot) *ring_slot = ring_value;
-  __syncthreads();
+  cta_sync<THREADS>();
 }
 
 // Level L-1 (and level 0 when L = 1): bits and directory; its nodes have
@@ -1152,10 +1170,10 @@ __device__ __forceinline__ void split_tile(const SplitArgs &a, const uint2 *tab,
   constexpr uint32_t T = 32 * WPT * THREADS;
   const uint32_t nv = (uint32_t)umin64(T, a.n - (uint64_t)tile * T);
   const SplitPassA<WPT> pa = split_pass_a<SB, THREADS, WPT>(a, sIn, nv, share_part, sm.wp, sm.wt);
-  __syncthreads();
+  cta_sync<THREADS>();
   const uint32_t pf = split_tile_rest<SB, THREADS, NC, WPT>(a, tab, tile, sIn, pa, sm);
   if (ring_slot) *ring_slot = ring_value;
-  __syncthreads();
+  cta_sync<THREADS>();
   split_flush_runs<NC>(a, sm.cnt, sm.run, sm.nc, pf);
 }
 
@@ -1537,10 +1555,10 @@ __device__ void tables_one_cta(const uint32_t *hist, uint32_t L, unsigned long l
       run += v[i];
     }
     carry += total;
-    __syncthreads();
+    cta_sync<THREADS>();
   }
   if (tid == 0) E[nbins] = carry;
-  __syncthreads();
+  cta_sync<THREADS>();
   for (uint32_t l = 0; l + 1 < L; ++l) {
     const uint32_t cnt = 1u << l, sh = L - l - 1;
     uint2 *tl = tab + (cnt - 1);
@@ -1563,7 +1581,7 @@ __device__ void tables_one_cta(const uint32_t *hist, uint32_t L, unsigned long l
         O += c1[i];
       }
       carry += total;
-      __syncthreads();
+      cta_sync<THREADS>();
     }
   }
 }

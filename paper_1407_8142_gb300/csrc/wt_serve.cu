@@ -28,6 +28,7 @@ namespace {
 
 constexpr uint32_t kSlotMaxTrees = 1024;   // requests per batch
 constexpr uint32_t kSlotMaxGroups = kSlotMaxTrees * (kMaxLevels + 2);
+constexpr uint32_t kSlotMaxHints = 1u << 20;  // group hints per batch (coarser for larger batches)
 
 double now_s() {
   using namespace std::chrono;
@@ -98,10 +99,12 @@ struct Slot {
   BTree *d_trees = nullptr;
   uint32_t *d_first = nullptr;
   uint2 *d_grp = nullptr;
+  uint32_t *d_hint = nullptr;
   // pinned host staging of the same
   BTree *h_trees = nullptr;
   uint32_t *h_first = nullptr;
   uint2 *h_grp = nullptr;
+  uint32_t *h_hint = nullptr;
 };
 
 }  // namespace
@@ -141,6 +144,10 @@ int launch_slot(wt_server *srv, Slot &s) {
   std::vector<uint32_t> first;
   std::vector<uint2> grp;
   const uint32_t items = batch_worklist(geo, first, grp);
+  std::vector<uint32_t> hint;
+  const uint32_t hint_shift = batch_hints(first, items, kSlotMaxHints, hint);
+  uint32_t max_sb = 1;
+  for (uint32_t i = 0; i < m; ++i) max_sb = std::max(max_sb, srv->reqs[s.ids[i]].d.symbol_bytes);
   for (uint32_t i = 0; i < m; ++i) {
     Request &r = srv->reqs[s.ids[i]];
     unsigned char *base = srv->d_arena + r.off;
@@ -177,7 +184,9 @@ int launch_slot(wt_server *srv, Slot &s) {
   }
   std::memcpy(s.h_first, first.data(), first.size() * 4);
   std::memcpy(s.h_grp, grp.data(), grp.size() * sizeof(uint2));
+  std::memcpy(s.h_hint, hint.data(), hint.size() * 4);
   if (cudaMemcpyAsync(s.d_trees, s.h_trees, m * sizeof(BTree), cudaMemcpyHostToDevice, s.st) != cudaSuccess ||
+      cudaMemcpyAsync(s.d_hint, s.h_hint, hint.size() * 4, cudaMemcpyHostToDevice, s.st) != cudaSuccess ||
       cudaMemcpyAsync(s.d_first, s.h_first, first.size() * 4, cudaMemcpyHostToDevice, s.st) != cudaSuccess ||
       cudaMemcpyAsync(s.d_grp, s.h_grp, grp.size() * sizeof(uint2), cudaMemcpyHostToDevice, s.st) != cudaSuccess ||
       cudaMemsetAsync(s.d_ctrl, 0, 64, s.st) != cudaSuccess)
@@ -186,13 +195,15 @@ int launch_slot(wt_server *srv, Slot &s) {
   a.trees = s.d_trees;
   a.grp_first = s.d_first;
   a.grp = s.d_grp;
+  a.hint = s.d_hint;
+  a.hint_shift = hint_shift;
   a.n_groups = (uint32_t)grp.size();
   a.n_items = items;
   a.ticket = s.d_ctrl;
   a.spin_limit = srv->cfg.spin_limit ? srv->cfg.spin_limit : (1u << 22);
   a.err = reinterpret_cast<int *>(s.d_ctrl + 1);
   a.t_start = reinterpret_cast<unsigned long long *>(s.d_ctrl + 2);
-  if (batch_launch(a, srv->threads, srv->sms, srv->cfg.ctas_per_sm, s.st) != cudaSuccess) return WT_ERR_CUDA;
+  if (batch_launch(a, srv->threads, max_sb, srv->sms, srv->cfg.ctas_per_sm, s.st) != cudaSuccess) return WT_ERR_CUDA;
   if (cudaEventRecord(s.ev, s.st) != cudaSuccess) return WT_ERR_CUDA;
   s.busy = true;
   ++srv->batches;
@@ -281,9 +292,11 @@ int wt_server_free(wt_server *srv) {
     cudaFree(s.d_trees);
     cudaFree(s.d_first);
     cudaFree(s.d_grp);
+    cudaFree(s.d_hint);
     cudaFreeHost(s.h_trees);
     cudaFreeHost(s.h_first);
     cudaFreeHost(s.h_grp);
+    cudaFreeHost(s.h_hint);
   }
   for (auto &kv : srv->reqs) delete kv.second.view;
   cudaFree(srv->d_arena);
@@ -320,9 +333,11 @@ int wt_server_create(uint64_t budget_bytes, uint32_t max_inflight, const wt_conf
         cudaMalloc(&s.d_trees, kSlotMaxTrees * sizeof(BTree)) != cudaSuccess ||
         cudaMalloc(&s.d_first, (kSlotMaxGroups + 1) * 4) != cudaSuccess ||
         cudaMalloc(&s.d_grp, kSlotMaxGroups * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&s.d_hint, kSlotMaxHints * 4) != cudaSuccess ||
         cudaMallocHost(&s.h_trees, kSlotMaxTrees * sizeof(BTree)) != cudaSuccess ||
         cudaMallocHost(&s.h_first, (kSlotMaxGroups + 1) * 4) != cudaSuccess ||
-        cudaMallocHost(&s.h_grp, kSlotMaxGroups * sizeof(uint2)) != cudaSuccess)
+        cudaMallocHost(&s.h_grp, kSlotMaxGroups * sizeof(uint2)) != cudaSuccess ||
+        cudaMallocHost(&s.h_hint, kSlotMaxHints * 4) != cudaSuccess)
       return fail(WT_ERR_OOM);
   }
   srv->worker = std::thread(worker_main, srv);
