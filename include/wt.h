@@ -150,6 +150,21 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
  */
 int wt_rebuild(wt_tree *tree, const void *d_seq, void *stream);
 
+/*
+ * Re-target `tree` to sequences of n symbols, n <= the n it was created
+ * with, reusing its device memory: a caller that builds many sequences of
+ * different lengths over one alphabet allocates one tree for the longest
+ * and resizes it before each wt_rebuild, with no cudaMalloc per sequence.
+ * The output layout follows the new n (wt_info); the contents of earlier
+ * builds are invalid afterwards.  The schedule chosen at creation (tile
+ * size, levels per pass, node counts) is kept; it builds any n.  Host-side
+ * only and immediate, except that n = 0 clears the directories with a
+ * synchronous cudaMemset.  The tree's last build must be complete (wt_sync)
+ * before the call.  Not for views (WT_ERR_ARG).
+ * Errors: WT_ERR_ARG (n above the creation size, NULL or a view), WT_ERR_CUDA.
+ */
+int wt_resize(wt_tree *tree, uint64_t n);
+
 /* wt_create followed by wt_rebuild. */
 int wt_build(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
              void *stream, wt_tree **out);

@@ -510,6 +510,7 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
     return WT_ERR_CUDA;
   }
   t->n = n;
+  t->cap_n = n;
   t->sigma = sigma;
   t->sb = symbol_bytes;
   t->L = L;
@@ -704,6 +705,31 @@ int wt_build_host(wt_tree *t, const void *h_seq, uint32_t *h_bits, uint64_t *h_r
   const int rc = wt_build_host_async(t, h_seq, h_bits, h_rank, stream);
   if (rc) return rc;
   return wt_sync(t);
+}
+
+int wt_resize(wt_tree *t, uint64_t n) {
+  if (!t || t->owner || n > t->cap_n) return WT_ERR_ARG;
+  // every size below grows with n at a fixed tile size, so the buffers
+  // allocated for cap_n hold them; the schedule chosen at creation (tile
+  // size, levels per pass, node counts) is kept: it builds any n
+  t->n = n;
+  t->NB = (n + 511) / 512;
+  t->W = 16 * t->NB;
+  t->NT = std::max<uint64_t>(1, (n + t->T - 1) / t->T);
+  t->NTf = std::max<uint64_t>(1, (n + t->tile_f - 1) / t->tile_f);
+  t->counts_per_level = t->NT + (t->NT >> 6) + 1 + (t->NT >> 12) + 1;
+  const bool tree = t->shape == WT_SHAPE_TREE;
+  const uint64_t hist_words = tree ? (1ull << t->L) : (t->fuse_k > 1 ? 256 : 0);
+  const uint64_t Lz = std::max<uint32_t>(t->L, 1);
+  t->ctrl_words = kCtrlWords + hist_words + Lz * t->counts_per_level;
+  ++t->build_count;  // the contents (and any query index) belong to the old n
+  t->sticky_error = 0;
+  if (n == 0) {
+    // an empty build leaves the directories as they are: they must read 0
+    WT_CUDA(cudaMemset(t->d_rank, 0, Lz * 8));
+    WT_CUDA(cudaMemset(t->d_zeros, 0, Lz * 8));
+  }
+  return WT_OK;
 }
 
 int wt_info(const wt_tree *t, wt_info_t *info) {

@@ -22,6 +22,7 @@ enum KernelKind : int32_t {
 
 struct wt_tree {
   uint64_t n = 0;
+  uint64_t cap_n = 0;             // the n the buffers were sized for (wt_resize keeps n <= cap_n)
   uint32_t sigma = 0, sb = 0, L = 0;
   uint32_t shape = WT_SHAPE_TREE;  // WT_SHAPE_TREE or WT_SHAPE_MATRIX
   // tree with a large alphabet: node sizes come from per-node counts kept by

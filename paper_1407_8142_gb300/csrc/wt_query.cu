@@ -335,7 +335,9 @@ int check_launch() {
 // falls back to a binary search over the whole directory.
 int ensure_sel_index(wt_tree *t, cudaStream_t st) {
   if (t->n == 0 || t->L == 0 || t->sel_for == t->build_count + 1) return WT_OK;
-  const uint64_t stride = (t->n / kSelSample) + 2;
+  // sized for the largest n the tree can be resized to, so that the index
+  // stays valid across wt_resize
+  const uint64_t stride = (std::max(t->n, t->cap_n) / kSelSample) + 2;
   if (!t->d_sel) {
     if (cudaMalloc(&t->d_sel, (uint64_t)t->L * 2 * stride * 4) != cudaSuccess) {
       (void)cudaGetLastError();

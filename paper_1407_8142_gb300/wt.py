@@ -80,6 +80,7 @@ SIGNATURES = {
     "wt_free": (ctypes.c_int, [P]),
     "wt_kernels_per_build": (ctypes.c_int, [P]),
     "wt_build_noalloc": (ctypes.c_int, [P, U64, U32, U32, P, P, P, P, P, P]),
+    "wt_resize": (ctypes.c_int, [P, U64]),
     "wt_batch_create": (ctypes.c_int, [P, U32, ctypes.POINTER(Config), ctypes.POINTER(P)]),
     "wt_batch_set_inputs": (ctypes.c_int, [P, P]),
     "wt_batch_build": (ctypes.c_int, [P, P]),
@@ -297,6 +298,14 @@ class WaveletTree:
                            bits.ctypes.data if bits is not None and bits.size else None,
                            rank.ctypes.data if rank is not None and rank.size else None, stream)
         return rc, bits, rank
+
+    def resize(self, n: int) -> "WaveletTree":
+        """Re-target the tree to n symbols (n <= its creation size), reusing
+        its device memory (wt_resize).  Waits for the last build first."""
+        self.sync()
+        _check(load().wt_resize(self.handle, n), "wt_resize")
+        self.n = n
+        return self
 
     def sync(self) -> int:
         return wt_sync(self.handle)

@@ -72,3 +72,9 @@ def test_noalloc_size_checks_cannot_wrap(lib):
     # sigma beyond 2^16 (17 levels) is beyond the fixed scratch
     assert lib.wt_build_noalloc(None, 10, (1 << 16) + 1, 4, None, None, None, None, None,
                                 None) == wt.WT_ERR_ARG
+
+
+def test_resize_checks_on_the_host(lib):
+    """wt_resize rejects a NULL tree before touching the device."""
+    from paper_1407_8142_gb300 import wt
+    assert lib.wt_resize(None, 10) == wt.WT_ERR_ARG

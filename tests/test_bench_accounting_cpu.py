@@ -63,21 +63,26 @@ def test_traffic_is_used_only_at_matching_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic() is None
 
 
-def test_theoretical_peak_from_device_properties(monkeypatch):
-    import torch
+def test_theoretical_peak_from_device_attributes(monkeypatch):
+    seen = []
 
-    class Props:
-        memory_clock_rate = 3996000   # kHz
-        memory_bus_width = 8192       # bits
+    def fake(idx, attrs):
+        seen.append((idx, tuple(attrs)))
+        return [3996000, 8192]  # kHz, bits
 
-    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev=0: Props())
+    monkeypatch.setattr(bench, "device_attributes", fake)
     assert bench.theoretical_hbm_gbs(0) == pytest.approx(2 * 3.996e9 * 8192 / 8 / 1e9)
-
-    class Missing:
-        pass
-
-    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev=0: Missing())
+    assert seen == [(0, (36, 37))]  # cudaDevAttrMemoryClockRate, cudaDevAttrGlobalMemoryBusWidth
+    monkeypatch.setattr(bench, "device_attributes", lambda idx, attrs: None)
     assert bench.theoretical_hbm_gbs(0) is None
+    monkeypatch.setattr(bench, "device_attributes", lambda idx, attrs: [0, 8192])
+    assert bench.theoretical_hbm_gbs(0) is None
+
+
+def test_cpu_model_is_readable():
+    cores, model = bench.host_info()
+    assert cores >= 1 and model and not model.startswith("0x")
+    assert bench.ARM_PARTS["0xd4f"] == "Arm Neoverse V2"
 
 
 def test_cpu_baseline_over_sequences():
