@@ -24,7 +24,48 @@ struct BTree {
   uint32_t *done;           // one completion counter per phase
   uint32_t phases;
   unsigned long long *t_done;  // global-timer stamp when the tree's last item completed
+  // node counts instead of a 2^L-bin histogram (large alphabets): the split
+  // of each level counts, per child node, the next level's ones into `hist`,
+  // and a node-table phase turns them into that level's tables
+  uint32_t nc;
+  uint32_t chunk_shift;     // node-table and leaf-start items cover 2^chunk_shift nodes
+  unsigned long long *status;  // look-back words of the node-table phases (cleared per build)
 };
+
+// What a phase of a tree does, and on which level.
+enum BatchPhaseKind : uint32_t {
+  kPhPrepass = 0, kPhTables = 1, kPhSplit = 2, kPhLeaf = 3, kPhNodeTables = 4, kPhLeafStarts = 5
+};
+struct PhaseInfo {
+  uint32_t kind, level;
+};
+
+// Phases of a tree with a histogram: 0 pre-pass, 1 tables, 2..L split
+// levels 0..L-2, L+1 last level.  With node counts (L >= 2): 0 pre-pass,
+// 2m+1 split of level m (m <= L-2), 2m node tables of level m (1 <= m <=
+// L-2), 2L-2 node starts of the last two levels, 2L-1 last level.
+__host__ __device__ __forceinline__ PhaseInfo batch_phase(uint32_t nc, uint32_t L, uint32_t ph) {
+  if (ph == 0) return {kPhPrepass, 0};
+  if (!nc) {
+    if (ph == 1) return {kPhTables, 0};
+    const uint32_t lv = ph - 2;
+    return {lv + 1 < L ? kPhSplit : kPhLeaf, lv};
+  }
+  if (ph == 2 * L - 1) return {kPhLeaf, L - 1};
+  if (ph == 2 * L - 2) return {kPhLeafStarts, L - 1};
+  if (ph & 1u) return {kPhSplit, (ph - 1) / 2};
+  return {kPhNodeTables, ph / 2};
+}
+
+// Items of a phase: tiles, one table item, or node chunks.
+__host__ __device__ __forceinline__ uint32_t batch_phase_items(uint32_t nc, uint32_t L, uint32_t NT,
+                                                              uint32_t chunk_shift, uint32_t ph) {
+  const PhaseInfo pi = batch_phase(nc, L, ph);
+  if (pi.kind == kPhTables) return 1u;
+  if (pi.kind == kPhNodeTables) return (((1u << pi.level) - 1u) >> chunk_shift) + 1u;
+  if (pi.kind == kPhLeafStarts) return (((1u << (L - 1)) - 1u) >> chunk_shift) + 1u;
+  return NT;
+}
 
 struct BatchArgs {
   const BTree *trees;
@@ -46,7 +87,7 @@ __device__ __forceinline__ unsigned long long global_timer() {
 }
 
 __device__ __forceinline__ uint32_t phase_items(const BTree &t, uint32_t phase) {
-  return phase == 1 ? 1u : t.NT;
+  return batch_phase_items(t.nc, t.L, t.NT, t.chunk_shift, phase);
 }
 
 __device__ __forceinline__ TileCounts tree_counts(const BTree &t, uint32_t level) {
@@ -72,9 +113,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // for the only level of a one-level tree; else the ping-pong buffer the
 // previous level wrote (whole tiles).
 __device__ __forceinline__ const uint8_t *item_input(const BTree &tr, uint32_t phase) {
-  const uint32_t level = phase >= 2 ? phase - 2 : 0;
-  if (phase == 0 || level == 0 || tr.L < 2) return tr.in;
-  return tr.buf[(level - 1) & 1];
+  const PhaseInfo pi = batch_phase(tr.nc, tr.L, phase);
+  if (pi.kind == kPhPrepass || pi.level == 0 || tr.L < 2) return tr.in;
+  return tr.buf[(pi.level - 1) & 1];
+}
+
+// Whether an item of the phase reads a tile of symbols.
+__device__ __forceinline__ bool phase_reads_tile(const BTree &tr, uint32_t phase) {
+  const uint32_t k = batch_phase(tr.nc, tr.L, phase).kind;
+  return k == kPhPrepass || k == kPhSplit || k == kPhLeaf;
 }
 
 // Input tiles in flight per block: three, or two when the batch holds
@@ -99,7 +146,7 @@ constexpr uint32_t batch_smem_bytes() {
   // split-run counters and the table scan's warp sums
   return batch_slots<MAXSB>() * 32u * THREADS * MAXSB + (THREADS / 32) * stage_bytes<MAXSB>() + 8u * THREADS +
          8u * (THREADS / 32) + batch_slots<MAXSB>() * (uint32_t)sizeof(BatchSlot) + 16u * batch_slots<MAXSB>() +
-         32u + 4u * 33u + 16u;
+         64u + 4u * 33u + 16u;
 }
 
 constexpr uint32_t kBatchHistSmem = 8192;  // histograms up to this many bins in shared memory
@@ -107,12 +154,12 @@ constexpr uint32_t kBatchHistSmem = 8192;  // histograms up to this many bins in
 // The work of one item (a tile of the pre-pass, of a split level or of the
 // last level) by the consumer warps; sIn holds the tile's symbols.
 template <int SB, int THREADS, int MAXSB>
-__device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint32_t share_part, uint8_t *sIn,
+__device__ void batch_tile(const BTree &tr, PhaseInfo pi, uint32_t tile, uint32_t share_part, uint8_t *sIn,
                            uint8_t *sStage, uint2 *sWP, uint2 *sWT, uint32_t *sMisc,
                            uint32_t spin_limit) {
   const uint32_t tid = threadIdx.x;
   const uint32_t L = tr.L;
-  if (phase == 0) {
+  if (pi.kind == kPhPrepass) {
     PrepassArgs a;
     a.in = tr.in;
     a.in_padded = 0;
@@ -128,7 +175,10 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint3
     uint32_t bad = 0;
     const uint32_t nbins = 1u << L;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(sStage);
-    if (nbins <= kHistBallotMaxBins) {
+    if (tr.nc) {
+      // node counts: no histogram, the range check and level 0's ones only
+      prepass_tile<SB, THREADS, kHistNone>(a, tile, sIn, nullptr, sMisc, bad, nullptr, 0);
+    } else if (nbins <= kHistBallotMaxBins) {
       // few bins: shared-memory atomics of a row would collide on them
       prepass_tile<SB, THREADS, kHistBallot>(a, tile, sIn, nullptr, sMisc, bad, nullptr, 0);
     } else if (nbins <= kBatchHistSmem && nbins * 4 <= (THREADS / 32) * stage_bytes<MAXSB>()) {
@@ -143,10 +193,10 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint3
     if (bad) latch_error(tr.err, WT_ERR_SYMBOL);
     return;
   }
-  const uint32_t level = phase - 2;  // split level, or L-1 for the last level
+  const uint32_t level = pi.level;
   const LevelOut lo{tr.bits + (uint64_t)level * tr.W, tr.rank + (uint64_t)level * (tr.NB + 1),
                     tr.zeros + level};
-  if (level + 1 < L) {
+  if (pi.kind == kPhSplit) {
     SplitArgs a;
     a.in = level == 0 ? tr.in : tr.buf[(level - 1) & 1];
     a.out = tr.buf[level & 1];
@@ -162,17 +212,40 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint3
     a.pshift = L - level;
     a.count_table = 0;
     a.tab_out = nullptr;
-    a.nones_next = nullptr;
+    a.nones_next = tr.nc ? tr.hist + ((2u << level) - 1) : nullptr;
     a.lo = lo;
     a.cin = tree_counts(tr, level);
     a.cout = tree_counts(tr, level + 1);
     a.ticket = nullptr;
     a.spin_limit = spin_limit;
     a.err = tr.err;
-    const SplitShared sm{sStage, sWP, sWT, sMisc, sMisc + 4, nullptr};
+    // sMisc: [0..3] run counters, [4..5] run starts, [6..7] the level-0
+    // table of a node-count tree, [8..10] node-count cache
+    uint2 *const sTab0 = reinterpret_cast<uint2 *>(sMisc + 6);
+    uint32_t *const sNc = sMisc + 8;
+    const SplitShared sm{sStage, sWP, sWT, sMisc, sMisc + 4, sNc};
     if (tid < 4) sMisc[tid] = 0;
+    if (tr.nc && level == 0 && tid < 32) {
+      // one node: its ones go after all zeros of the level, which are n
+      // minus the level's ones (the top tier of its tile counts)
+      const uint32_t ones = counts_total_warp(a.cin, tr.NT);
+      if (tid == 0) {
+        *sTab0 = make_uint2(0u, tr.n - ones);
+        if (tile == 0) tr.tab[0] = *sTab0;  // the node tables of level 1 read it
+      }
+    }
+    if (tid == 0) sNc[0] = 0xFFFFFFFFu;
     cta_sync<THREADS>();
-    split_tile<SB, THREADS, false>(a, a.tab, tile, sIn, share_part, sm, nullptr, 0);
+    const uint2 *tab = (tr.nc && level == 0) ? sTab0 : a.tab;
+    if (tr.nc) {
+      split_tile<SB, THREADS, true>(a, tab, tile, sIn, share_part, sm, nullptr, 0);
+      if (tid == 0 && sNc[0] != 0xFFFFFFFFu) {  // the item's cached node counts
+        if (sNc[1]) atomicAdd(&a.nones_next[2 * sNc[0]], sNc[1]);
+        if (sNc[2]) atomicAdd(&a.nones_next[2 * sNc[0] + 1], sNc[2]);
+      }
+    } else {
+      split_tile<SB, THREADS, false>(a, tab, tile, sIn, share_part, sm, nullptr, 0);
+    }
   } else {
     LeafArgs a;
     a.in = L >= 2 ? tr.buf[(L - 2) & 1] : tr.in;
@@ -188,6 +261,106 @@ __device__ void batch_tile(const BTree &tr, uint32_t phase, uint32_t tile, uint3
     a.spin_limit = spin_limit;
     a.err = tr.err;
     leaf_tile<SB, THREADS>(a, tile, sIn, share_part, sWT, nullptr, 0);
+  }
+}
+
+// Node tables of level m of a node-count tree, for the nodes of chunk
+// `chunk` (2^chunk_shift nodes, 8 per thread): the same tables as the
+// single-tree build's node-table kernel, with the scan across chunks by
+// look-back over the tree's status words of the level.  With s(q) = start
+// of node q and c(q) its ones: O_m(q) = sum of c over nodes < q, tab_m[q] =
+// {O_m(q), s(q+1) - c(q) - O_m(q)}; an odd node starts where its parent's
+// 1-child does, an even node where its parent does (written before).
+template <int THREADS>
+__device__ void batch_node_tables(const BTree &tr, uint32_t m, uint32_t chunk, uint32_t *s_warp,
+                                  uint32_t spin_limit) {
+  constexpr uint32_t ITEMS = 8;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t cnt = 1u << m, sh = tr.L - m;
+  const uint32_t *ones = tr.hist + (cnt - 1);
+  const uint2 *tab_prev = tr.tab + ((cnt >> 1) - 1);
+  uint2 *tab = tr.tab + (cnt - 1);
+  unsigned long long *E = tr.node_start;
+  const uint32_t base = (chunk << tr.chunk_shift) + tid * ITEMS;
+  auto start_of = [&](uint32_t q) -> uint32_t {  // s(q), 0 <= q <= 2^m
+    if (q >= cnt) return tr.n;
+    if (q & 1u) {
+      const uint2 t = tab_prev[q >> 1];
+      return t.x + t.y;
+    }
+    return (uint32_t)E[(uint64_t)q << sh];
+  };
+  uint32_t c[ITEMS];
+  uint32_t sum = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; ++i) {
+    c[i] = base + i < cnt ? __ldcg(&ones[base + i]) : 0u;
+    sum += c[i];
+  }
+  uint32_t total;
+  const uint32_t excl = block_exclusive_scan<THREADS>(sum, s_warp, &total);
+  // the level's look-back words follow those of the levels before it
+  uint32_t first = 0;
+  for (uint32_t l = 1; l < m; ++l) first += (((1u << l) - 1u) >> tr.chunk_shift) + 1u;
+  if (tid < 32) {
+    Lookback lb;
+    lb.status = tr.status + first;
+    lb.epoch = 1;  // the words are cleared before every build
+    lb.spin_limit = spin_limit;
+    lb.skip = 0;
+    lb.err = tr.err;
+    const uint32_t P = lookback(lb, chunk, 0, total);
+    if (tid == 0) s_warp[32] = P;
+  }
+  cta_sync<THREADS>();
+  uint32_t O = s_warp[32] + excl;
+#pragma unroll
+  for (uint32_t i = 0; i < ITEMS; ++i) {
+    const uint32_t q = base + i;
+    if (q < cnt) {
+      if (q & 1u) E[(uint64_t)q << sh] = start_of(q);
+      tab[q] = make_uint2(O, start_of(q + 1) - c[i] - O);
+    }
+    O += c[i];
+  }
+  if (m == 1 && chunk == 0 && tid == 0) {
+    E[0] = 0;
+    E[1ull << tr.L] = tr.n;
+  }
+}
+
+// Node starts of the last two levels of a node-count tree, for the nodes of
+// level L-1 in chunk `chunk`: node q starts at E[2q] (odd q: where its
+// parent's 1-child starts) and its 1-child, symbol value 2q+1, at
+// s(q+1) - c(q).  Also E[0] = 0 and E[2^L] = n.
+template <int THREADS>
+__device__ void batch_leaf_starts(const BTree &tr, uint32_t chunk) {
+  const uint32_t L = tr.L;
+  const uint32_t cnt = 1u << (L - 1);
+  const uint32_t *ones = tr.hist + (cnt - 1);
+  const uint2 *tab_prev = tr.tab + ((cnt >> 1) - 1);
+  unsigned long long *E = tr.node_start;
+  const uint32_t q0 = chunk << tr.chunk_shift;
+  const uint32_t q1 = min(cnt, q0 + (1u << tr.chunk_shift));
+  for (uint32_t q = q0 + threadIdx.x; q < q1; q += THREADS) {
+    uint32_t next;
+    if (q + 1 >= cnt) {
+      next = tr.n;
+    } else if ((q + 1) & 1u) {
+      const uint2 t = tab_prev[(q + 1) >> 1];
+      next = t.x + t.y;
+    } else {
+      next = (uint32_t)E[2ull * (q + 1)];
+    }
+    if (q & 1u) {
+      const uint2 t = tab_prev[q >> 1];
+      E[2ull * q] = t.x + t.y;
+    }
+    E[2ull * q + 1] = next - __ldcg(&ones[q]);
+    if (q == 0) {
+      E[0] = 0;
+      E[1ull << L] = tr.n;
+    }
   }
 }
 
@@ -326,12 +499,13 @@ __device__ __forceinline__ void batch_producer(const BatchArgs &a, uint8_t *sBuf
     flags = __shfl_sync(0xFFFFFFFFu, flags, 0);
     __syncwarp();  // the dependency seen complete before the count loads
     uint32_t prefix = 0;
-    if (phase >= 2 && !flags) {
+    const PhaseInfo pi = batch_phase(tr.nc, tr.L, phase);
+    if ((pi.kind == kPhSplit || pi.kind == kPhLeaf) && !flags) {
       // the tile's exclusive ones-prefix from the level's tile counts: the
       // previous tile's prefix plus its count when this item follows it,
       // else a sum of up to (tile >> 12) + 126 terms; the tile's own count
       // is loaded for the next item
-      const TileCounts c = tree_counts(tr, phase - 2);
+      const TileCounts c = tree_counts(tr, pi.level);
       if (g == pv_g && tile == pv_tile + 1) {
         prefix = pv_prefix + pv_c0;
       } else {
@@ -349,7 +523,7 @@ __device__ __forceinline__ void batch_producer(const BatchArgs &a, uint8_t *sBuf
       sSlot[s].tile = tile;
       sSlot[s].flags = flags;
       sSlot[s].prefix = prefix;
-      if (phase != 1 && flags == 0) {
+      if (phase_reads_tile(tr, phase) && flags == 0) {
         const uint8_t *in = item_input(tr, phase);
         const uint64_t start = (uint64_t)tile * T;
         const uint32_t nv = (uint32_t)umin64(T, tr.n - start);
@@ -403,8 +577,8 @@ __global__ void __launch_bounds__(THREADS + 32, batch_min_blocks<THREADS, MAXSB>
   BatchSlot *const sSlot = reinterpret_cast<BatchSlot *>(sWT + NW);
   uint64_t *const full = reinterpret_cast<uint64_t *>(sSlot + R);
   uint64_t *const empty = full + R;
-  uint32_t *const sMisc = reinterpret_cast<uint32_t *>(empty + R);  // split-run counters and starts
-  uint32_t *const s_warp = sMisc + 8;                               // 33 words
+  uint32_t *const sMisc = reinterpret_cast<uint32_t *>(empty + R);  // split-run counters, starts, ...
+  uint32_t *const s_warp = sMisc + 16;                              // 33 words
   const uint32_t tid = threadIdx.x;
   if (tid == 0) {
     for (uint32_t i = 0; i < R; ++i) {
@@ -432,9 +606,14 @@ __global__ void __launch_bounds__(THREADS + 32, batch_min_blocks<THREADS, MAXSB>
     if (sl.flags & kSlotEnd) return;
     const BTree &tr = sl.tr;
     const uint32_t phase = sl.phase, tile = sl.tile;
+    const PhaseInfo pi = batch_phase(tr.nc, tr.L, phase);
     if (!(sl.flags & kSlotSkip)) {
-      if (phase == 1) {
+      if (pi.kind == kPhTables) {
         tables_one_cta<THREADS>(tr.hist, tr.L, tr.node_start, tr.tab, s_warp);
+      } else if (pi.kind == kPhNodeTables) {
+        batch_node_tables<THREADS>(tr, pi.level, tile, s_warp, a.spin_limit);
+      } else if (pi.kind == kPhLeafStarts) {
+        batch_leaf_starts<THREADS>(tr, tile);
       } else {
         uint8_t *const sIn = sBuf + s * TB;
         const uint8_t *in = item_input(tr, phase);
@@ -447,14 +626,14 @@ __global__ void __launch_bounds__(THREADS + 32, batch_min_blocks<THREADS, MAXSB>
         }
         const uint32_t share = tid == 0 ? sl.prefix : 0u;
         switch (tr.sb) {
-          case 1: batch_tile<1, THREADS, MAXSB>(tr, phase, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit); break;
+          case 1: batch_tile<1, THREADS, MAXSB>(tr, pi, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit); break;
           case 2:
             if constexpr (MAXSB >= 2)
-              batch_tile<2, THREADS, MAXSB>(tr, phase, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit);
+              batch_tile<2, THREADS, MAXSB>(tr, pi, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit);
             break;
           default:
             if constexpr (MAXSB >= 4)
-              batch_tile<4, THREADS, MAXSB>(tr, phase, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit);
+              batch_tile<4, THREADS, MAXSB>(tr, pi, tile, share, sIn, sStage, sWP, sWT, sMisc, a.spin_limit);
             break;
         }
       }
@@ -475,6 +654,9 @@ struct BatchGeo {
   uint64_t n, NB, W, NT, nbins, cpl;
   uint64_t bits, rank, zeros, ns, tab, buf, ctrl;
   uint32_t L, phases;
+  bool nc;               // node counts instead of a histogram
+  uint32_t chunk_shift;  // nodes per node-table item: 2^chunk_shift
+  uint64_t status;       // look-back words of the node-table phases
 };
 
 inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -506,9 +688,17 @@ inline bool batch_geo(const wt_seq_desc &d, uint32_t threads, BatchGeo &g) {
   g.tab = al256(std::max<uint64_t>(1, g.nbins / 2) * 8);
   g.buf = g.L >= 2 ? al256(g.NT * T * d.symbol_bytes + 16) : 0;
   g.cpl = g.NT + (g.NT >> 6) + 1 + (g.NT >> 12) + 1;
-  g.phases = g.L >= 1 ? g.L + 2 : 2;
-  // control block: error word, histogram, tile counts, phase counters, stamp
-  g.ctrl = al256((1 + g.nbins + Lz * g.cpl + g.phases) * 4 + 16);
+  // large alphabets: per-node counts instead of the 2^L-bin histogram
+  g.nc = g.L >= 2 && g.nbins > kBatchHistSmem;
+  g.chunk_shift = 0;
+  while ((1u << g.chunk_shift) < 8u * threads) ++g.chunk_shift;  // 8 nodes per consumer thread
+  g.status = 0;
+  if (g.nc)
+    for (uint32_t l = 1; l + 1 < g.L; ++l) g.status += (((1ull << l) - 1) >> g.chunk_shift) + 1;
+  g.phases = g.nc ? 2 * g.L : (g.L >= 1 ? g.L + 2 : 2);
+  // control block: error word, histogram (or node counts), tile counts,
+  // phase counters, stamp, look-back words of the node-table phases
+  g.ctrl = al256((1 + g.nbins + Lz * g.cpl + g.phases) * 4 + 16 + 8 * g.status + 8);
   return true;
 }
 
@@ -544,6 +734,9 @@ inline BTree batch_tree(const wt_seq_desc &d, const BatchGeo &g, unsigned char *
   t.phases = g.phases;
   t.t_done = reinterpret_cast<unsigned long long *>(
       (reinterpret_cast<uintptr_t>(t.done + g.phases) + 7) & ~uintptr_t(7));
+  t.status = t.t_done + 1;
+  t.nc = g.nc ? 1u : 0u;
+  t.chunk_shift = g.chunk_shift;
   t.n = (uint32_t)g.n;
   t.L = g.L;
   t.sigma = d.sigma;
@@ -568,7 +761,7 @@ inline uint32_t batch_worklist(const std::vector<BatchGeo> &geo, std::vector<uin
       if (ph >= geo[i].phases) continue;
       first.push_back(items);
       grp.push_back(make_uint2(i, ph));
-      items += ph == 1 ? 1u : (uint32_t)geo[i].NT;
+      items += batch_phase_items(geo[i].nc, geo[i].L, (uint32_t)geo[i].NT, geo[i].chunk_shift, ph);
     }
   first.push_back(items);
   return items;
