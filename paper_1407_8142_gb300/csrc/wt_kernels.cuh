@@ -790,6 +790,19 @@ __device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint3
     const uint32_t gzq = tb.x + Zw + zs;         // destination of the node's zeros
     const uint32_t goq = tb.y + Ow + (f - zs);   // destination of the node's ones
     const uint32_t zrun = ze - zs, orun = (fe - ze) - (f - zs);
+    // The runs, node by node and zeros before ones, go to children 2p, 2p+1,
+    // 2p+2, ... of T_{l+1}: their destinations rise, so the next level's ones
+    // are added up per destination tile and flushed once per change of tile.
+    uint32_t cdt = 0xFFFFFFFFu, ccnt = 0;  // running destination tile and its ones (lane 0)
+    auto tile_add = [&](uint32_t t, uint32_t c) {
+      if (t == cdt) {
+        ccnt += c;
+      } else {
+        if (ccnt && cdt < NT) counts_add(cout, cdt, ccnt);
+        cdt = t;
+        ccnt = c;
+      }
+    };
     for (uint32_t q = 0; q < span; ++q) {
 #pragma unroll
       for (uint32_t part = 0; part < 2; ++part) {
@@ -812,12 +825,13 @@ __device__ __forceinline__ void split_multi_node(uint8_t *out, uint32_t n, uint3
         ca = __reduce_add_sync(0xFFFFFFFFu, ca);
         cb = __reduce_add_sync(0xFFFFFFFFu, cb);
         if (lane == 0) {
-          if (ca && dt < NT) counts_add(cout, dt, ca);
-          if (cb && dt + 1 < NT) counts_add(cout, dt + 1, cb);
+          if (ca) tile_add(dt, ca);
+          if (cb) tile_add(dt + 1, cb);
           if (NC && nones_next && ca + cb) atomicAdd(&nones_next[2 * (wpf + q) + part], ca + cb);
         }
       }
     }
+    if (lane == 0 && ccnt && cdt < NT) counts_add(cout, cdt, ccnt);
   } else {
     // More than 32 nodes in the warp: each symbol goes to the zero or
     // one range of its own node.  Zeros (then ones) are staged in node
