@@ -331,9 +331,12 @@ int wt_build_batch(const wt_seq_desc *descs, const void *const *d_seqs, uint32_t
  * A worker thread admits queued requests in arrival order as soon as a
  * request's footprint (its input copy, outputs, scratch and control block)
  * fits in a device arena of `budget_bytes` (allocated once at creation) and
- * one of `max_inflight` streams is free; all requests admissible at that
- * moment form one batch (one launch of the batched build kernel).  Batches
- * on different streams overlap on the device, so requests that arrive while
+ * one of `max_inflight` streams is free; the requests admissible at that
+ * moment with fewer than 2^20 symbols and sigma <= 2^13 form one batch (one
+ * launch of the batched build kernel); every other request is built alone
+ * with the single-tree schedule of wt_build (the library's choice of tile
+ * size and levels per pass), its buffers in its arena region.  Work on
+ * different streams overlaps on the device, so requests that arrive while
  * others run start as soon as memory and a stream free up.  Results stay in
  * the arena until released.  Each result is bit-identical to a wt_build of
  * the same input.  A completed result holds its memory until it is

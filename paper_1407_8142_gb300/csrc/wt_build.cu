@@ -483,12 +483,10 @@ extern "C" {
 
 }  // extern "C"
 
-namespace {
+namespace wtk {
 
-int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
-                 uint32_t shape, wt_tree **out) {
-  if (!out) return WT_ERR_ARG;
-  *out = nullptr;
+int tree_shape(wt_tree *t, uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+               uint32_t shape) {
   if (!(symbol_bytes == 1 || symbol_bytes == 2 || symbol_bytes == 4)) return WT_ERR_ARG;
   if (sigma == 0 || (uint64_t)sigma > (1ull << (8 * symbol_bytes))) return WT_ERR_ARG;
   if (n >= (1ull << 32)) return WT_ERR_ARG;
@@ -498,15 +496,11 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
                                     cfg->tile_threads == 512))
     return WT_ERR_ARG;
   if (cfg && cfg->levels_per_pass > kMaxLevelsPerPass) return WT_ERR_ARG;
-
-  wt_tree *t = new (std::nothrow) wt_tree();
-  if (!t) return WT_ERR_OOM;
   if (cfg) t->cfg = *cfg;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     (void)cudaGetLastError();
-    delete t;
     return WT_ERR_CUDA;
   }
   t->n = n;
@@ -531,47 +525,115 @@ int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_con
   t->NT = std::max<uint64_t>(1, (n + t->T - 1) / t->T);
   t->tile_f = fused_tile_symbols(symbol_bytes);
   t->NTf = std::max<uint64_t>(1, (n + t->tile_f - 1) / t->tile_f);
+  const bool tree = shape == WT_SHAPE_TREE;
+  // histogram words: the tree's 2^L bins, or the matrix's digit counts of its k-level passes
+  const uint64_t hist_words = tree ? 1ull << L : (t->fuse_k > 1 ? 256 : 0);
+  const uint64_t Lz = std::max<uint32_t>(L, 1);
+  t->counts_per_level = t->NT + (t->NT >> 6) + 1 + (t->NT >> 12) + 1;
+  t->ctrl_words = kCtrlWords + hist_words + Lz * t->counts_per_level;
+  // whole tiles of either schedule
+  t->buf_bytes = std::max(t->NT * t->T, t->NTf * t->tile_f) * symbol_bytes + 16;
+  t->status_n = std::max<uint64_t>({t->NT, (uint64_t)hist_blocks(L), (uint64_t)tables_blocks(L), 1});
+  if (t->fuse_k > 1)
+    t->status_n = std::max<uint64_t>({t->status_n, (uint64_t)fused_tables_blocks(L, t->fuse_k),
+                                      (uint64_t)t->fuse_k * fused_dir_chunks(t->NB)});
+  return WT_OK;
+}
 
+TreeLayout tree_layout(const wt_tree *t) {
+  TreeLayout ly{};
+  const bool tree = t->shape == WT_SHAPE_TREE;
+  const uint64_t nbins = tree ? 1ull << t->L : 0;
+  const size_t Lz = std::max<uint32_t>(t->L, 1);
+  ly.bits = std::max<size_t>(4, Lz * t->W * 4);
+  ly.rank = Lz * (t->NB + 1) * 8;
+  ly.zeros = Lz * 8;
+  if (tree) {
+    ly.node_start = (nbins + 1) * 8;
+    ly.tab = std::max<uint64_t>(1, nbins / 2) * sizeof(uint2);
+    if (t->fuse_k > 1 && t->L >= 2) ly.ftab = nbins * 4;
+  }
+  if (t->fuse_k > 1) ly.fcount = (2 * t->NTf << t->fuse_k) * 4;
+  ly.ctrl = t->ctrl_words * 4;
+  ly.buf = t->L >= 2 ? t->buf_bytes : 0;
+  ly.status = t->status_n * 8;
+  return ly;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t tree_region_bytes(const TreeLayout &ly) {
+  return al256(ly.bits) + al256(ly.rank) + al256(ly.zeros) + al256(ly.node_start) + al256(ly.tab) +
+         al256(ly.ftab) + al256(ly.fcount) + al256(ly.ctrl) + 2 * al256(ly.buf) + al256(ly.status);
+}
+
+void tree_bind_derived(wt_tree *t) {
+  const uint64_t hist_words = t->shape == WT_SHAPE_TREE ? 1ull << t->L : (t->fuse_k > 1 ? 256 : 0);
+  t->d_hist = t->d_ctrl + kCtrlWords;
+  t->d_counts = t->d_hist + hist_words;
+}
+
+void tree_bind(wt_tree *t, const TreeLayout &ly, unsigned char *base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> unsigned char * {
+    if (!bytes) return nullptr;
+    unsigned char *p = base + off;
+    off += al256(bytes);
+    return p;
+  };
+  t->d_bits = reinterpret_cast<uint32_t *>(take(ly.bits));
+  t->d_rank = reinterpret_cast<unsigned long long *>(take(ly.rank));
+  t->d_zeros = reinterpret_cast<unsigned long long *>(take(ly.zeros));
+  t->d_node_start = reinterpret_cast<unsigned long long *>(take(ly.node_start));
+  t->d_tab = reinterpret_cast<uint2 *>(take(ly.tab));
+  t->d_ftab = reinterpret_cast<uint32_t *>(take(ly.ftab));
+  t->d_fcount = reinterpret_cast<uint32_t *>(take(ly.fcount));
+  t->d_ctrl = reinterpret_cast<uint32_t *>(take(ly.ctrl));
+  t->d_buf[0] = take(ly.buf);
+  t->d_buf[1] = take(ly.buf);
+  t->d_status = reinterpret_cast<unsigned long long *>(take(ly.status));
+  tree_bind_derived(t);
+}
+
+}  // namespace wtk
+
+namespace {
+
+int create_shape(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+                 uint32_t shape, wt_tree **out) {
+  if (!out) return WT_ERR_ARG;
+  *out = nullptr;
+  wt_tree *t = new (std::nothrow) wt_tree();
+  if (!t) return WT_ERR_OOM;
+  if (int rc = tree_shape(t, n, sigma, symbol_bytes, cfg, shape)) {
+    delete t;
+    return rc;
+  }
   auto fail = [&](cudaError_t e) {
     (void)cudaGetLastError();
     release(t);
     delete t;
     return cuda_fail(e);
   };
+  const TreeLayout ly = tree_layout(t);
   cudaError_t e;
-  const bool tree = shape == WT_SHAPE_TREE;
-  const uint64_t nbins = tree ? 1ull << L : 0;  // the matrix needs no histogram or node tables
-  // histogram words: the tree's 2^L bins, or the matrix's digit counts of its k-level passes
-  const uint64_t hist_words = tree ? nbins : (t->fuse_k > 1 ? 256 : 0);
-  const size_t Lz = std::max<uint32_t>(L, 1);
-  if ((e = cudaMalloc(&t->d_bits, std::max<size_t>(4, Lz * t->W * 4)))) return fail(e);
-  if ((e = cudaMalloc(&t->d_rank, Lz * (t->NB + 1) * 8))) return fail(e);
-  if ((e = cudaMalloc(&t->d_zeros, Lz * 8))) return fail(e);
-  if (tree) {
-    if ((e = cudaMalloc(&t->d_node_start, (nbins + 1) * 8))) return fail(e);
-    if ((e = cudaMalloc(&t->d_tab, std::max<uint64_t>(1, nbins / 2) * sizeof(uint2)))) return fail(e);
-    if (t->fuse_k > 1 && L >= 2 && (e = cudaMalloc(&t->d_ftab, nbins * 4))) return fail(e);
+  if ((e = cudaMalloc(&t->d_bits, ly.bits))) return fail(e);
+  if ((e = cudaMalloc(&t->d_rank, ly.rank))) return fail(e);
+  if ((e = cudaMalloc(&t->d_zeros, ly.zeros))) return fail(e);
+  if (ly.node_start && (e = cudaMalloc(&t->d_node_start, ly.node_start))) return fail(e);
+  if (ly.tab && (e = cudaMalloc(&t->d_tab, ly.tab))) return fail(e);
+  if (ly.ftab && (e = cudaMalloc(&t->d_ftab, ly.ftab))) return fail(e);
+  if (ly.fcount && (e = cudaMalloc(&t->d_fcount, ly.fcount))) return fail(e);
+  if ((e = cudaMalloc(&t->d_ctrl, ly.ctrl))) return fail(e);
+  if (ly.buf) {
+    if ((e = cudaMalloc(&t->d_buf[0], ly.buf))) return fail(e);
+    if ((e = cudaMalloc(&t->d_buf[1], ly.buf))) return fail(e);
   }
-  if (t->fuse_k > 1 && (e = cudaMalloc(&t->d_fcount, (2 * t->NTf << t->fuse_k) * 4))) return fail(e);
-  t->counts_per_level = t->NT + (t->NT >> 6) + 1 + (t->NT >> 12) + 1;
-  t->ctrl_words = kCtrlWords + hist_words + (uint64_t)Lz * t->counts_per_level;
-  if ((e = cudaMalloc(&t->d_ctrl, t->ctrl_words * 4))) return fail(e);
-  t->d_hist = t->d_ctrl + kCtrlWords;
-  t->d_counts = t->d_hist + hist_words;
-  // whole tiles of either schedule
-  t->buf_bytes = std::max(t->NT * t->T, t->NTf * t->tile_f) * symbol_bytes + 16;
-  if (L >= 2) {
-    if ((e = cudaMalloc(&t->d_buf[0], t->buf_bytes))) return fail(e);
-    if ((e = cudaMalloc(&t->d_buf[1], t->buf_bytes))) return fail(e);
-  }
-  t->status_n = std::max<uint64_t>({t->NT, (uint64_t)hist_blocks(L), (uint64_t)tables_blocks(L), 1});
-  if (t->fuse_k > 1)
-    t->status_n = std::max<uint64_t>({t->status_n, (uint64_t)fused_tables_blocks(L, t->fuse_k),
-                                      (uint64_t)t->fuse_k * fused_dir_chunks(t->NB)});
-  if ((e = cudaMalloc(&t->d_status, t->status_n * 8))) return fail(e);
-  if ((e = cudaMemset(t->d_status, 0, t->status_n * 8))) return fail(e);
-  if ((e = cudaMemset(t->d_zeros, 0, Lz * 8))) return fail(e);
-  if ((e = cudaMemset(t->d_rank, 0, Lz * (t->NB + 1) * 8))) return fail(e);
+  if ((e = cudaMalloc(&t->d_status, ly.status))) return fail(e);
+  tree_bind_derived(t);
+  if ((e = cudaMemset(t->d_status, 0, ly.status))) return fail(e);
+  if ((e = cudaMemset(t->d_zeros, 0, ly.zeros))) return fail(e);
+  if ((e = cudaMemset(t->d_rank, 0, ly.rank))) return fail(e);
   *out = t;
   return WT_OK;
 }
@@ -592,7 +654,15 @@ int wt_matrix_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt
 
 int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
   if (!t || (!d_seq && t->n) || t->owner) return WT_ERR_ARG;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return wtk::tree_rebuild(t, d_seq, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace wtk {
+
+int tree_rebuild(wt_tree *t, const void *d_seq, cudaStream_t st) {
+  if (!t || (!d_seq && t->n)) return WT_ERR_ARG;
   t->stream = st;
   t->sticky_error = 0;
   ++t->build_count;
@@ -625,6 +695,10 @@ int wt_rebuild(wt_tree *t, const void *d_seq, void *stream) {
   }
   return WT_ERR_ARG;
 }
+
+}  // namespace wtk
+
+extern "C" {
 
 int wt_build_ex(const void *d_seq, uint64_t n, uint32_t sigma, uint32_t symbol_bytes,
                 const wt_config *cfg, void *stream, wt_tree **out) {

@@ -87,3 +87,26 @@ struct wt_tree {
     if (d_sel) cudaFree(d_sel);
   }
 };
+
+namespace wtk {
+
+// Device buffers of a tree (bytes; 0 = not needed), from its shape fields.
+struct TreeLayout {
+  size_t bits, rank, zeros, node_start, tab, ftab, fcount, ctrl, buf, status;
+};
+
+// Check the arguments and fill the shape fields of t (schedule, tile sizes,
+// buffer sizes) as wt_create / wt_matrix_create do, without allocating.
+int tree_shape(wt_tree *t, uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config *cfg,
+               uint32_t shape);
+TreeLayout tree_layout(const wt_tree *t);
+// All of a tree's buffers in one region (256-byte aligned pieces).
+size_t tree_region_bytes(const TreeLayout &ly);
+// Point t's buffers into the region at base (tree_region_bytes bytes).
+void tree_bind(wt_tree *t, const TreeLayout &ly, unsigned char *base);
+// The pointers derived from d_ctrl (histogram, tile counts).
+void tree_bind_derived(wt_tree *t);
+// Enqueue a build of t from d_seq on st (wt_rebuild without its ownership check).
+int tree_rebuild(wt_tree *t, const void *d_seq, cudaStream_t st);
+
+}  // namespace wtk

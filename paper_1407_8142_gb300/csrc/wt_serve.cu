@@ -29,6 +29,12 @@ namespace {
 constexpr uint32_t kSlotMaxTrees = 1024;   // requests per batch
 constexpr uint32_t kSlotMaxGroups = kSlotMaxTrees * (kMaxLevels + 2);
 constexpr uint32_t kSlotMaxHints = 1u << 20;  // group hints per batch (coarser for larger batches)
+// Requests of at least this many symbols, and requests whose alphabet the
+// batched kernel would build with node counts (2L phases whose hand-offs
+// dominate a short tree's latency), are built alone, with the single-tree
+// schedule (whole-GPU passes, levels per pass as the library chooses) in
+// their own arena region; the others share batched launches.
+constexpr uint64_t kSingleMinSymbols = 1ull << 20;
 
 double now_s() {
   using namespace std::chrono;
@@ -86,7 +92,8 @@ struct Request {
   double t_submit = 0, t_done = 0;
   int state = 0;              // 0 queued, 1 in flight, 2 done
   int status = 0;
-  wt_tree *view = nullptr;
+  bool single = false;        // built alone with the single-tree schedule
+  wt_tree *view = nullptr;    // the result; for a single build also the tree that builds it
 };
 
 struct Slot {
@@ -136,9 +143,32 @@ struct wt_server {
 
 namespace {
 
+// Launch one request built alone on slot s: its input and the tree's
+// buffers in its arena region, the single-tree schedule on the slot's stream.
+int launch_single(wt_server *srv, Slot &s, Request &r) {
+  unsigned char *base = srv->d_arena + r.off;
+  const size_t in_bytes = al256(r.d.n * r.d.symbol_bytes);
+  wt_tree *v = r.view;
+  const TreeLayout ly = tree_layout(v);
+  tree_bind(v, ly, base + in_bytes);
+  v->owner = srv;
+  v->sticky_error = 0;
+  if (cudaMemcpyAsync(base, r.h_seq, r.d.n * r.d.symbol_bytes, cudaMemcpyHostToDevice, s.st) != cudaSuccess ||
+      cudaMemsetAsync(v->d_status, 0, ly.status, s.st) != cudaSuccess ||
+      cudaMemsetAsync(v->d_rank, 0, ly.rank, s.st) != cudaSuccess ||
+      cudaMemsetAsync(v->d_zeros, 0, ly.zeros, s.st) != cudaSuccess)
+    return WT_ERR_CUDA;
+  if (int rc = tree_rebuild(v, base, s.st)) return rc;
+  if (cudaEventRecord(s.ev, s.st) != cudaSuccess) return WT_ERR_CUDA;
+  s.busy = true;
+  ++srv->batches;
+  return WT_OK;
+}
+
 // Launch one batch of admitted requests on slot s (worker thread, lock held).
 int launch_slot(wt_server *srv, Slot &s) {
   const uint32_t m = (uint32_t)s.ids.size();
+  if (m == 1 && srv->reqs[s.ids[0]].single) return launch_single(srv, s, srv->reqs[s.ids[0]]);
   std::vector<BatchGeo> geo(m);
   for (uint32_t i = 0; i < m; ++i) geo[i] = srv->reqs[s.ids[i]].geo;
   std::vector<uint32_t> first;
@@ -246,6 +276,9 @@ void worker_main(wt_server *srv) {
     if (free_slot && !srv->queue.empty()) {
       while (!srv->queue.empty() && free_slot->ids.size() < kSlotMaxTrees) {
         Request &r = srv->reqs[srv->queue.front()];
+        // a single-schedule request is launched alone (it waits for the next
+        // slot when this one already holds batched requests)
+        if (!free_slot->ids.empty() && (r.single || srv->reqs[free_slot->ids[0]].single)) break;
         size_t off;
         if (!srv->arena.alloc(r.bytes, off)) break;  // wait for memory to free up
         r.off = off;
@@ -352,10 +385,24 @@ int wt_server_submit(wt_server *srv, const void *h_seq, uint64_t n, uint32_t sig
   r.h_seq = h_seq;
   r.d = wt_seq_desc{n, sigma, symbol_bytes};
   if (!batch_geo(r.d, srv->threads, r.geo)) return WT_ERR_ARG;
-  r.bytes = al256(n * symbol_bytes) + batch_mem_bytes(r.geo) + r.geo.ctrl;
-  if (r.bytes > srv->budget) return WT_ERR_ARG;  // can never be admitted
   r.view = new (std::nothrow) wt_tree();
   if (!r.view) return WT_ERR_OOM;
+  r.single = n >= kSingleMinSymbols || r.geo.nc;
+  if (r.single) {
+    wt_config c{};
+    c.spin_limit = srv->cfg.spin_limit;
+    if (int rc = tree_shape(r.view, n, sigma, symbol_bytes, &c, WT_SHAPE_TREE)) {
+      delete r.view;
+      return rc;
+    }
+    r.bytes = al256(n * symbol_bytes) + tree_region_bytes(tree_layout(r.view));
+  } else {
+    r.bytes = al256(n * symbol_bytes) + batch_mem_bytes(r.geo) + r.geo.ctrl;
+  }
+  if (r.bytes > srv->budget) {  // can never be admitted
+    delete r.view;
+    return WT_ERR_ARG;
+  }
   r.t_submit = now_s();
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->fatal) {
