@@ -240,6 +240,8 @@ def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int, k: in
     NB = (n + 511) // 512
     bits = 16 * NB * 4
     directory = 8 * (NB + 1)
+    if kind == "directory" and k == 1:  # the last level's directory after a last-pair pass
+        return bits + directory
     if kind in ("fused", "directory", "tile_count"):
         l0 = level_index * k
         kp = max(0, min(k, L - l0))
@@ -252,6 +254,8 @@ def algorithmic_bytes(kind: str, level_index: int, n: int, b: int, L: int, k: in
         return n * b
     if kind == "split":               # reads T_l, writes T_{l+1}, B_l and its directory
         return 2 * n * b + bits + directory
+    if kind == "last_pair":           # reads T_(L-2), writes B_(L-2), its directory and B_(L-1)
+        return n * b + 2 * bits + directory
     if kind == "leaf":
         return n * b + bits + directory
     if kind == "hist_scan":
@@ -425,7 +429,9 @@ def main_ours(args):
     # split pass (one level per pass) or the k-level pass
     fused = K > 1
     main_kind = "fused" if fused else "split"
-    n_main = (L + K - 1) // K if fused else max(L - 1, 0)
+    # launches of the dominant kernel per build (one level per pass: L - 1
+    # splits, or L - 2 when the last two levels take one pass)
+    n_main = max(1, sum(1 for kind, _ in prof if kind == main_kind) // max(args.steps, 1))
     per_kind = {}
     main_bytes = main_ms = 0.0
     main_launches = 0
@@ -455,6 +461,9 @@ def main_ours(args):
                            + algorithmic_bytes("tile_count", j, n, sb, L, K) for j in range(n_main))
         if matrix:
             build_bytes -= algorithmic_bytes("prepass", 0, n, sb, L)  # the first count kernel checks the range
+    elif "last_pair" in per_kind:
+        build_bytes += (n_main * algorithmic_bytes("split", 0, n, sb, L) + algorithmic_bytes("last_pair", 0, n, sb, L)
+                        + algorithmic_bytes("directory", 0, n, sb, L, 1))
     else:
         build_bytes += (sum(algorithmic_bytes("split", l, n, sb, L) for l in range(L - 1))
                         + algorithmic_bytes("leaf", L - 1, n, sb, L))

@@ -259,7 +259,9 @@ int wt_select(const wt_tree *tree, const uint32_t *d_c, const uint64_t *d_k, uin
  * number of launches recorded in the window and fills up to `cap` entries of
  * ms[] with each launch's duration and kind[] with its kind: 0 pre-pass,
  * 1 node starts (histogram scan, or the last two levels' starts from node
- * counts), 2 node tables, 3 split pass, 4 last-level pass.
+ * counts), 2 node tables, 3 split pass, 4 last-level pass, 5 k-level pass,
+ * 6 directories, 7 digit counts, 8 their scan, 9 the last two levels in one
+ * pass.
  * wt_profile(tree, 0) stops recording.
  */
 int wt_profile(wt_tree *tree, int enable);

@@ -253,6 +253,60 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   return WT_OK;
 }
 
+// Levels L-2 and L-1 in one pass over T_{L-2} (k_lastpair): the arguments
+// of the split pass over level L-2, and level L-1's row, zeroed first.
+template <int SB, int THREADS>
+int launch_lastpair(Launcher &ln, const uint8_t *in, bool in_padded) {
+  wt_tree *t = ln.t;
+  const uint32_t level = t->L - 2;
+  LastPairArgs la;
+  SplitArgs &a = la.s;
+  a.in = in;
+  a.out = nullptr;
+  a.in_padded = in_padded ? 1 : 0;
+  a.n = (uint32_t)t->n;
+  a.L = t->L;
+  a.level = level;
+  a.NT = (uint32_t)t->NT;
+  a.NB = (uint32_t)t->NB;
+  a.log2T = 5 + (uint32_t)__builtin_ctz(THREADS);
+  a.W = t->W;
+  const bool matrix = t->shape == WT_SHAPE_MATRIX;
+  const bool count_table = matrix || (t->node_counts && level == 0);
+  a.tab = count_table ? nullptr : t->d_tab + ((1u << level) - 1);
+  a.pshift = matrix ? t->L : t->L - level;
+  a.count_table = count_table ? 1 : 0;
+  a.tab_out = (t->node_counts && level == 0) ? t->d_tab : nullptr;
+  a.nones_next = t->node_counts ? t->d_hist + ((2u << level) - 1) : nullptr;
+  a.lo = ln.out(level);
+  a.cin = ln.counts(level);
+  a.cout = ln.counts(level);  // unused: no T_{L-1}
+  a.ticket = ln.ticket();
+  a.spin_limit = ln.spin();
+  a.err = ln.err();
+  la.row_next = t->d_bits + (uint64_t)(level + 1) * t->W;
+  WT_CUDA(cudaMemsetAsync(la.row_next, 0, t->W * 4, ln.st));
+  constexpr int WPT = (SB == 1 && THREADS == 512) ? 2 : 1;
+  constexpr int CTA = THREADS / WPT;
+  auto kern = t->node_counts ? k_lastpair<SB, CTA, true, WPT> : k_lastpair<SB, CTA, false, WPT>;
+  constexpr uint32_t sm = lastpair_smem_bytes<SB, CTA, WPT>();
+  if (int rc = set_smem(kern, sm)) return rc;
+  const int grid = std::min<int>((int)t->NT, occupancy(kern, CTA, sm, t->sms, t->cfg.ctas_per_sm));
+  ln.before(kLastPair);
+  kern<<<std::max(grid, 1), CTA, sm, ln.st>>>(la);
+  ln.after();
+  ++ln.pass;
+  WT_CUDA(cudaGetLastError());
+  return WT_OK;
+}
+
+// Whether the build takes its last two levels in one pass: when the nodes of
+// level L-2 are long (64 Ki symbols on average), so that almost every warp
+// lies in one node and writes its level-(L-1) bits as two runs.
+bool use_lastpair(const wt_tree *t) {
+  return t->fuse_k == 1 && t->L >= 2 && (t->n >> (t->L - 2)) >= (1ull << 16);
+}
+
 // Node starts E[v] = symbols whose top log2(nbins) bits are < v.
 int launch_hist_scan(Launcher &ln, uint32_t nbins) {
   wt_tree *t = ln.t;
@@ -400,7 +454,9 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
   if (t->L == 0) return WT_OK;
   const uint8_t *in = seq;
   bool padded = seq_padded;
-  for (uint32_t l = 0; l + 1 < t->L; ++l) {
+  const bool pair = use_lastpair(t);
+  const uint32_t last_split = pair ? t->L - 2 : t->L - 1;  // levels below it take one split pass each
+  for (uint32_t l = 0; l < last_split; ++l) {
     // with node counts, the tables of level l come from the pass over l-1
     if (t->node_counts && l >= 1 && (rc = launch_node_tables(ln, l))) return rc;
     uint8_t *out = static_cast<uint8_t *>(t->d_buf[l & 1]);
@@ -409,8 +465,21 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
     in = out;
     padded = true;
   }
-  if (t->node_counts && (rc = launch_node_tables(ln, t->L - 1))) return rc;
-  if ((rc = launch_leaf<SB, THREADS>(ln, in, padded, t->L - 1))) return rc;
+  if (pair) {
+    const uint32_t m = t->L - 2;
+    if (t->node_counts && m >= 1 && (rc = launch_node_tables(ln, m))) return rc;
+    if ((rc = launch_lastpair<SB, THREADS>(ln, in, padded))) return rc;
+    if (t->record_levels) WT_CUDA(cudaEventRecord(t->level_ev[m], st));
+    if (t->node_counts && (rc = launch_node_tables(ln, t->L - 1))) return rc;
+    ln.before(kDirectory);
+    rc = fused_dir(t, st, t->L - 1, 1, ln.lb(), ln.ticket());
+    ln.after();
+    ++ln.pass;
+    if (rc) return rc;
+  } else {
+    if (t->node_counts && (rc = launch_node_tables(ln, t->L - 1))) return rc;
+    if ((rc = launch_leaf<SB, THREADS>(ln, in, padded, t->L - 1))) return rc;
+  }
   if (t->record_levels) WT_CUDA(cudaEventRecord(t->level_ev[t->L - 1], st));
   return WT_OK;
 }

@@ -103,30 +103,6 @@ struct FusedArgs {
 __device__ __forceinline__ uint32_t gran_of(uint32_t h) { return 31u - __clz(h + 1u); }
 __device__ __forceinline__ uint32_t rev_bits(uint32_t c, uint32_t i) { return i ? __brev(c) >> (32u - i) : 0u; }
 
-// Copy bits [src, src+len) of the tile bitmap w (w[0] and w[NWD+1] are zero
-// pads, bit x at w[1 + x/32]) to bits [g, g+len) of `row`, by one warp.
-// Words the run covers entirely are stored; the two end words are shared
-// with other runs and are or-ed in (the row was zeroed before the pass).
-__device__ __forceinline__ void warp_bit_run(const uint32_t *w, uint32_t src, uint32_t *row, uint64_t g,
-                                             uint32_t len) {
-  if (!len) return;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t w0 = g >> 5, w1 = (g + len - 1) >> 5;
-  for (uint64_t ow = w0 + lane; ow <= w1; ow += 32) {
-    const long long sp = (long long)src + (long long)(32 * ow) - (long long)g;  // >= src - 31
-    const long long wi = sp >> 5;                                               // >= -1
-    const uint32_t lo = w[1 + wi], hi = w[2 + wi];
-    uint32_t val = __funnelshift_r(lo, hi, (uint32_t)(sp & 31));
-    const uint64_t base = 32 * ow;
-    const uint32_t qlo = g > base ? (uint32_t)(g - base) : 0u;
-    const uint32_t qhi = (uint32_t)umin64(32, g + len - base);
-    const uint32_t mask = (qhi == 32 ? ~0u : ((1u << qhi) - 1u)) & ~((1u << qlo) - 1u);
-    val &= mask;
-    if (mask == ~0u) row[ow] = val;
-    else if (val) atomicOr(&row[ow], val);
-  }
-}
-
 // Phase 1 of a round: this warp's V rows of the image into v[] (masked to
 // L bits on the first round), and the ballot of bit `sh` of each row; lane r
 // returns row r's word.  Positions at or past nv read as 0 (bit 0).

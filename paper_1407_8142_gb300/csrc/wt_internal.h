@@ -15,7 +15,7 @@ constexpr uint32_t kMaxProfiled = 2048;  // kernel launches recorded per profili
 
 enum KernelKind : int32_t {
   kPrepass = 0, kHistScan = 1, kTables = 2, kSplit = 3, kLeaf = 4, kFused = 5, kDirectory = 6,
-  kTileCount = 7, kTileScan = 8
+  kTileCount = 7, kTileScan = 8, kLastPair = 9
 };
 
 }  // namespace wtk

@@ -1335,6 +1335,282 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
   }
 }
 
+// ------------------------------------------------------------------ last two levels in one pass
+// Copy bits [src, src+len) of the tile bitmap w (w[0] and w[NWD+1] are zero
+// pads, bit x at w[1 + x/32]) to bits [g, g+len) of `row`, by one warp.
+// Words the run covers entirely are stored; the two end words are shared
+// with other runs and are or-ed in (the row was zeroed before the pass).
+__device__ __forceinline__ void warp_bit_run(const uint32_t *w, uint32_t src, uint32_t *row, uint64_t g,
+                                             uint32_t len) {
+  if (!len) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t w0 = g >> 5, w1 = (g + len - 1) >> 5;
+  for (uint64_t ow = w0 + lane; ow <= w1; ow += 32) {
+    const long long sp = (long long)src + (long long)(32 * ow) - (long long)g;  // >= src - 31
+    const long long wi = sp >> 5;                                               // >= -1
+    const uint32_t lo = w[1 + wi], hi = w[2 + wi];
+    uint32_t val = __funnelshift_r(lo, hi, (uint32_t)(sp & 31));
+    const uint64_t base = 32 * ow;
+    const uint32_t qlo = g > base ? (uint32_t)(g - base) : 0u;
+    const uint32_t qhi = (uint32_t)umin64(32, g + len - base);
+    const uint32_t mask = (qhi == 32 ? ~0u : ((1u << qhi) - 1u)) & ~((1u << qlo) - 1u);
+    val &= mask;
+    if (mask == ~0u) row[ow] = val;
+    else if (val) atomicOr(&row[ow], val);
+  }
+}
+
+// The last two levels in one pass over T_{L-2} (no T_{L-1} is written).
+// Level L-2's bits and directory are written as by the split pass.  Each
+// symbol's bit of level L-1 belongs at the position the split would move
+// the symbol to: within a warp lying in one node, the level-(L-1) bits of
+// its zeros, in order, form one run that starts where its zeros would go,
+// and those of its ones another.  So a thread compacts its words' level-
+// (L-1) bits into those of its zeros and those of its ones (a 256-entry
+// table per 4-bit nibble of value and mask), the warp assembles the two
+// bit streams in shared memory, and writes them as bit runs (the row is
+// zeroed before the pass; each run's end words are or-ed in).  A warp
+// spanning several nodes writes each of its level-(L-1) one bits at its
+// own position.  The directory of level L-1 is a separate pass.
+struct LastPairArgs {
+  SplitArgs s;          // as for the split pass over level L-2 (out, cout unused)
+  uint32_t *row_next;   // bitmap row of level L-1 (zeroed)
+};
+
+template <int SB, int WPT>
+__host__ __device__ constexpr uint32_t lastpair_stage_words() { return 2u * (32u * WPT + 2u); }
+
+// Node counts of level L-1 are kept per block in shared memory for up to
+// this many nodes of level L-2 (two counters each), and flushed once.
+constexpr uint32_t kLastPairSmemNodes = 1024;
+
+template <int SB, int THREADS, int WPT = 1>
+constexpr uint32_t lastpair_smem_bytes() {
+  // two input tiles, per warp two bit streams (with a zero pad word at each
+  // end), per-word {bit word, prefix}, two sets of per-warp {ones, share},
+  // the level table, the nibble table, node counters, mbarriers and tickets
+  return 2u * 32u * WPT * THREADS * SB + (THREADS / 32) * lastpair_stage_words<SB, WPT>() * 4u +
+         8u * WPT * THREADS + 16u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 256u +
+         8u * kLastPairSmemNodes + 128u;
+}
+
+template <int SB, int THREADS, int WPT = 1>
+constexpr int lastpair_min_blocks() {
+  constexpr uint32_t by_smem = 232448u / (lastpair_smem_bytes<SB, THREADS, WPT>() + 1024u);
+  constexpr uint32_t by_warps = 2048u / THREADS;
+  constexpr uint32_t r = by_smem < by_warps ? by_smem : by_warps;
+  return (int)(r > 5 ? 5 : (r ? r : 1u));
+}
+
+template <int SB, int THREADS, bool NC, int WPT = 1>
+__global__ void __launch_bounds__(THREADS, lastpair_min_blocks<SB, THREADS, WPT>()) k_lastpair(LastPairArgs la) {
+  using Sym = typename SymT<SB>::type;
+  constexpr uint32_t T = 32 * WPT * THREADS;
+  constexpr uint32_t NW = THREADS / 32;
+  constexpr uint32_t SPW = 1024 * WPT;          // symbols per warp
+  constexpr uint32_t SW = 32 * WPT + 2;         // words of one bit stream, with two pads
+  const SplitArgs &a = la.s;
+  extern __shared__ __align__(128) uint8_t smem[];
+  TilePipe<SB, THREADS, 2, WPT> pipe;
+  pipe.sIn0 = smem;
+  pipe.sIn1 = smem + pipe.TB;
+  uint32_t *const sStream = reinterpret_cast<uint32_t *>(smem + 2 * pipe.TB);  // per warp: zeros' bits, ones' bits
+  uint2 *const sWP = reinterpret_cast<uint2 *>(sStream + NW * 2 * SW);
+  uint2 *const sWT = sWP + WPT * THREADS;         // 2 sets
+  uint2 *const sTab = sWT + 2 * NW;
+  uint8_t *const sLut = reinterpret_cast<uint8_t *>(sTab + tab_smem_nodes<SB>());
+  uint32_t *const sNC = reinterpret_cast<uint32_t *>(sLut + 256);  // ones of child 2p + bit at [2p + bit]
+  pipe.bar = reinterpret_cast<uint64_t *>(sNC + 2 * kLastPairSmemNodes);
+  pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
+  pipe.in = a.in;
+  pipe.in_padded = a.in_padded;
+  pipe.n = a.n;
+  pipe.NT = a.NT;
+  pipe.ticket = a.ticket;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t nodes = 1u << (a.L - a.pshift);
+  const bool tab_smem = nodes <= tab_smem_nodes<SB>();
+  const uint2 *const tab = tab_smem ? sTab : a.tab;
+  const uint32_t k = a.L - 1 - a.level, k1 = k - 1;
+  const uint32_t lmask = (1u << a.L) - 1u;
+
+  // nibble table: entry (m << 4) | v holds the bits of v where m is 0,
+  // compacted in order (low nibble), and those where m is 1 (high nibble)
+  for (uint32_t e = tid; e < 256; e += THREADS) {
+    const uint32_t m = e >> 4, v = e & 15u;
+    uint32_t z = 0, o = 0, nz = 0, no = 0;
+    for (uint32_t j = 0; j < 4; ++j) {
+      const uint32_t b = (v >> j) & 1u;
+      if ((m >> j) & 1u) o |= b << no++;
+      else z |= b << nz++;
+    }
+    sLut[e] = (uint8_t)(z | (o << 4));
+  }
+  if (a.count_table) {
+    if (tid < 32) {
+      const uint32_t ones = counts_total_warp(a.cin, a.NT);
+      if (tid == 0) {
+        sTab[0] = make_uint2(0u, a.n - ones);
+        if (a.tab_out && blockIdx.x == 0) a.tab_out[0] = sTab[0];
+      }
+    }
+  } else if (tab_smem) {
+    for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
+  }
+  // the next level's ones per child node: in shared memory when the level
+  // has few nodes (then every warp of a node adds to the same counters)
+  const bool nc_smem = NC && a.nones_next && nodes <= kLastPairSmemNodes;
+  if (nc_smem)
+    for (uint32_t i = tid; i < 2 * nodes; i += THREADS) sNC[i] = 0;
+  auto nc_add = [&](uint32_t child, uint32_t c) {
+    if (nc_smem) atomicAdd(&sNC[child], c);
+    else atomicAdd(&a.nones_next[child], c);
+  };
+  uint32_t *const zs = sStream + warp * 2 * SW;  // this warp's zeros' bits: bit x at zs[1 + x / 32]
+  uint32_t *const os = zs + SW;                  // its ones' bits
+  for (uint32_t i = lane; i < 2 * SW; i += 32) zs[i] = 0;
+  if (tid == 0) pipe.prologue();
+  __syncthreads();
+  PrefixLoads pre = prefix_loads<THREADS>(a.cin, pipe.ring[0], a.NT);
+
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = pipe.ring[it % 3];
+    if (tile >= a.NT) break;
+    const uint32_t nxt = pipe.ring[(it + 1) % 3];
+    uint32_t nn = 0;
+    if (tid == 0) nn = atomicAdd(a.ticket, 1u);  // the ticket of tile it+2
+    const PrefixLoads pre_next = prefix_loads<THREADS>(a.cin, nxt, a.NT);
+    const bool ok = pipe.wait(it, a.spin_limit, a.err);
+    const uint64_t start = (uint64_t)tile * T;
+    const uint32_t nv = (uint32_t)umin64(T, a.n - start);
+    uint8_t *const sIn = pipe.data(it);
+    if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
+    const uint32_t par = it & 1u;
+    uint2 *const wt = sWT + par * NW;
+    const SplitPassA<WPT> pa = split_pass_a<SB, THREADS, WPT>(a, sIn, nv, pre.sum(), sWP, wt);
+    if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) mbar_wait_bounded(&pipe.bar[it & 1], (it >> 1) & 1u, a.spin_limit, a.err);
+      __syncthreads();
+      break;
+    }
+    if (tid == 0 && nxt < a.NT) {
+      fence_proxy_async_smem();
+      pipe.issue(nxt, (it + 1) & 1);
+    }
+    // level L-2: bits and directory, as in the split pass
+    const uint2 wv = lane < NW ? wt[lane] : make_uint2(0, 0);
+    const uint32_t Pw = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wv.x : 0u);  // ones before the warp
+    const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, wv.x);
+    const uint32_t R = __reduce_add_sync(0xFFFFFFFFu, wv.y);                       // ones before the tile
+    const uint32_t my0 = 32 * WPT * tid;
+#pragma unroll
+    for (int i = 0; i < WPT; ++i) {
+      const uint64_t widx = (uint64_t)tile * (WPT * THREADS) + WPT * tid + i;
+      if (widx < a.W) a.lo.bits[widx] = pa.word[i];
+      if ((widx & 15) == 0 && start + my0 + 32 * i < a.n) a.lo.rank[(start + my0 + 32 * i) >> 9] = R + Pw + pa.pw[i];
+    }
+    if (tile == a.NT - 1 && tid == 0) {
+      a.lo.rank[a.NB] = R + total;
+      *a.lo.zeros = (unsigned long long)(a.n - (R + total));
+    }
+    // level L-1: this thread's bits split into those of its zeros and of its
+    // ones, each in order, appended to the warp's two streams
+    const uint32_t seg = SPW * warp;
+    const uint32_t nvw = nv > seg ? min(nv - seg, SPW) : 0u;
+    const uint32_t tw = __shfl_sync(0xFFFFFFFFu, pa.incl, 31);  // ones of the warp
+    const uint32_t nzw = nvw - tw;
+    {
+      unsigned long long zacc = 0, oacc = 0;
+      uint32_t zf = 0, of = 0;
+#pragma unroll
+      for (int i = 0; i < WPT; ++i) {
+        const uint32_t vm = valid_mask(my0 + 32 * i, nv);
+        const uint32_t w1 = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k1) & vm;
+        const uint32_t w0 = pa.word[i];
+#pragma unroll
+        for (uint32_t g = 0; g < 8; ++g) {
+          const uint32_t mn = (w0 >> (4 * g)) & 15u, vn = (w1 >> (4 * g)) & 15u;
+          const uint32_t vmn = (vm >> (4 * g)) & 15u;  // positions past n are neither zeros nor ones
+          const uint32_t r = sLut[(mn << 4) | vn];
+          zacc |= (unsigned long long)(r & 15u) << zf;
+          oacc |= (unsigned long long)(r >> 4) << of;
+          const uint32_t c1 = __popc(mn);
+          zf += __popc(vmn) - c1;
+          of += c1;
+        }
+      }
+      // zeros before this thread within the warp: its position in the warp
+      // minus the ones before it
+      const uint32_t zb = 32 * WPT * lane - pa.pw[0], ob = pa.pw[0];
+      auto put = [&](uint32_t *s, uint32_t at, unsigned long long bits, uint32_t len) {
+        if (!len) return;
+        const uint32_t w = at >> 5, sh = at & 31u;
+        const uint32_t lo = (uint32_t)bits, hi = (uint32_t)(bits >> 32);
+        atomicOr(&s[1 + w], lo << sh);
+        if (sh + len > 32) atomicOr(&s[2 + w], __funnelshift_l(lo, hi, sh));
+        if (sh + len > 64) atomicOr(&s[3 + w], hi >> (32 - sh));
+      };
+      if (nvw) {
+        put(zs, zb, zacc, zf);
+        put(os, ob, oacc, of);
+      }
+    }
+    __syncwarp();
+    // the warp's node range (its segment is in node order)
+    const Sym *sInS = reinterpret_cast<const Sym *>(sIn);
+    const uint32_t Zw = (uint32_t)start - R + seg - Pw;  // zeros of level L-2 before the warp
+    const uint32_t Ow = R + Pw;                          // ones of level L-2 before the warp
+    if (nvw) {
+      const uint32_t wpf = ((uint32_t)sInS[seg] & lmask) >> a.pshift;
+      const uint32_t wpl = ((uint32_t)sInS[seg + nvw - 1] & lmask) >> a.pshift;
+      if (wpf == wpl) {
+        const uint2 tb = tab[wpf];
+        const uint64_t gz = (uint64_t)tb.x + Zw, go = (uint64_t)tb.y + Ow;
+        if (nzw && gz + nzw <= a.n) warp_bit_run(zs, 0, la.row_next, gz, nzw);
+        if (tw && go + tw <= a.n) warp_bit_run(os, 0, la.row_next, go, tw);
+        if (NC && a.nones_next) {
+          uint32_t cz = 0, co = 0;
+          for (uint32_t i = lane; i < 32 * WPT; i += 32) {
+            cz += __popc(zs[1 + i]);
+            co += __popc(os[1 + i]);
+          }
+          cz = __reduce_add_sync(0xFFFFFFFFu, cz);
+          co = __reduce_add_sync(0xFFFFFFFFu, co);
+          if (lane == 0) {
+            if (cz) nc_add(2 * wpf, cz);
+            if (co) nc_add(2 * wpf + 1, co);
+          }
+        }
+      } else {
+        // several nodes: each level-(L-1) one bit to its own position
+        for (uint32_t x = lane; x < nvw; x += 32) {
+          const uint32_t wi = (seg + x) >> 5, bi = x & 31u;
+          const uint2 wp = sWP[wi];
+          const uint32_t onesb = wp.y + __popc(wp.x & ((1u << bi) - 1u));  // ones before x within the warp
+          const uint32_t s = (uint32_t)sInS[seg + x];
+          if ((s >> k1) & 1u) {
+            const uint32_t p = (s & lmask) >> a.pshift;
+            const uint2 tb = tab[p];
+            const bool one = (wp.x >> bi) & 1u;
+            const uint64_t d = one ? (uint64_t)tb.y + Ow + onesb : (uint64_t)tb.x + Zw + (x - onesb);
+            if (d < a.n) atomicOr(&la.row_next[d >> 5], 1u << (d & 31u));
+            if (NC && a.nones_next) nc_add(2 * p + (one ? 1u : 0u), 1u);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < 2 * SW; i += 32) zs[i] = 0;  // the streams of the next tile
+    pre = pre_next;
+  }
+  if (nc_smem) {
+    __syncthreads();
+    for (uint32_t i = tid; i < 2 * nodes; i += THREADS)
+      if (sNC[i]) atomicAdd(&a.nones_next[i], sNC[i]);
+  }
+}
+
 // ------------------------------------------------------------------ tables
 struct ScanArgs {
   const uint32_t *hist;

@@ -27,7 +27,7 @@ ERROR_NAMES = {WT_ERR_ARG: "WT_ERR_ARG", WT_ERR_OOM: "WT_ERR_OOM", WT_ERR_CUDA: 
                WT_ERR_SYMBOL: "WT_ERR_SYMBOL", WT_ERR_TIMEOUT: "WT_ERR_TIMEOUT"}
 
 KERNEL_KINDS = {0: "prepass", 1: "hist_scan", 2: "tables", 3: "split", 4: "leaf", 5: "fused",
-                6: "directory", 7: "tile_count", 8: "tile_scan"}
+                6: "directory", 7: "tile_count", 8: "tile_scan", 9: "last_pair"}
 WT_SHAPE_TREE = 0
 WT_SHAPE_MATRIX = 1
 
