@@ -92,3 +92,11 @@ def test_cpu_baseline_over_sequences():
     assert r["kind"] == "oracle" and r["cores"] == 1
     assert r["sample"].startswith("first 3 sequences (15003 symbols)")
     assert r["value"] > 0 and r["host_cores"] >= 1 and r["cpu_model"]
+
+
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_last_pair_pass_bytes(b):
+    # one pass over T_(L-2) writes level L-2's bitmap and directory and level
+    # L-1's bitmap; level L-1's directory is a separate one-level pass
+    assert bench.algorithmic_bytes("last_pair", 6, N, b, 8) == N * b + 2 * bits(N) + directory(N)
+    assert bench.algorithmic_bytes("directory", 7, N, b, 8, 1) == bits(N) + directory(N)
