@@ -73,6 +73,7 @@ struct BatchArgs {
   const uint2 *grp;           // n_groups: {tree, phase}
   const uint32_t *hint;       // group of item i << hint_shift, for every such item
   uint32_t hint_shift;
+  uint32_t chunk;             // consecutive items per ticket (1..kBatchChunk)
   uint32_t n_groups, n_items;
   uint32_t *ticket;
   uint32_t spin_limit;
@@ -143,13 +144,17 @@ constexpr uint32_t batch_smem_bytes() {
   // the ring of input tiles (symbols of up to MAXSB bytes), per-warp staging
   // (also the shared histogram of the pre-pass), {word, prefix} per thread,
   // per-warp {ones, share}, slot descriptors, full and empty mbarriers,
-  // split-run counters and the table scan's warp sums
+  // split-run counters, the table scan's warp sums and the partition
+  // selectors of 1-byte symbols
   return batch_slots<MAXSB>() * 32u * THREADS * MAXSB + (THREADS / 32) * stage_bytes<MAXSB>() + 8u * THREADS +
          8u * (THREADS / 32) + batch_slots<MAXSB>() * (uint32_t)sizeof(BatchSlot) + 16u * batch_slots<MAXSB>() +
-         64u + 4u * 33u + 16u;
+         64u + 4u * 33u + 16u + 1024u;
 }
 
 constexpr uint32_t kBatchHistSmem = 8192;  // histograms up to this many bins in shared memory
+// Word offset, from the split-run counters, of the 256 partition selectors
+// (after the counters and the table scan's 33 warp sums).
+constexpr uint32_t kBatchPermWord = 52;
 
 // The work of one item (a tile of the pre-pass, of a split level or of the
 // last level) by the consumer warps; sIn holds the tile's symbols.
@@ -223,7 +228,7 @@ __device__ void batch_tile(const BTree &tr, PhaseInfo pi, uint32_t tile, uint32_
     // table of a node-count tree, [8..10] node-count cache
     uint2 *const sTab0 = reinterpret_cast<uint2 *>(sMisc + 6);
     uint32_t *const sNc = sMisc + 8;
-    const SplitShared sm{sStage, sWP, sWT, sMisc, sMisc + 4, sNc};
+    const SplitShared sm{sStage, sWP, sWT, sMisc, sMisc + 4, sNc, SB == 1 ? sMisc + kBatchPermWord : nullptr};
     if (tid < 4) sMisc[tid] = 0;
     if (tr.nc && level == 0 && tid < 32) {
       // one node: its ones go after all zeros of the level, which are n
@@ -364,9 +369,12 @@ __device__ void batch_leaf_starts(const BTree &tr, uint32_t chunk) {
   }
 }
 
-// Items a producer takes per ticket: consecutive items mostly share a group
-// (tree and phase), so one group search, one descriptor and one dependency
-// wait serve several items.
+// Items a producer takes per ticket, at most: consecutive items mostly share
+// a group (tree and phase), so one group search, one descriptor and one
+// dependency wait serve several items.  batch_launch takes fewer (items /
+// (8 x blocks), at least one) when the batch has few items per block, so
+// that a phase of a small tree is spread over as many blocks as it has
+// tiles.
 constexpr uint32_t kBatchChunk = 4;
 
 // Publish the completion of the item a slot held (one thread of the
@@ -379,7 +387,7 @@ __device__ __forceinline__ void batch_publish(const BatchSlot &sl) {
   if (sl.phase + 1 == sl.tr.phases && prev + 1 == phase_items(sl.tr, sl.phase)) *sl.tr.t_done = global_timer();
 }
 
-// The producer warp: takes kBatchChunk consecutive items per ticket, finds
+// The producer warp: takes a.chunk consecutive items per ticket, finds
 // each item's group (a hint per 2^hint_shift items, then a warp-wide search
 // of the next 32 group starts; consecutive items of one group reuse it),
 // copies the tree's descriptor into the next free slot, waits (bounded)
@@ -398,7 +406,7 @@ __device__ __forceinline__ void batch_producer(const BatchArgs &a, uint8_t *sBuf
   const uint32_t lane = threadIdx.x & 31;
   uint32_t item = 0, left = 0;               // the current chunk
   uint32_t next_chunk = 0;                   // lane 0: the ticket of the chunk after it (fetched early)
-  if (lane == 0) next_chunk = atomicAdd(a.ticket, kBatchChunk);
+  if (lane == 0) next_chunk = atomicAdd(a.ticket, a.chunk);
   uint32_t g = 0, g_lo = 1, g_hi = 0;        // the current group and its items [g_lo, g_hi)
   uint32_t ready = 0xFFFFFFFFu;              // group whose dependency was seen complete
   // the previous split or last-level item: its group, tile, prefix and own count
@@ -440,10 +448,10 @@ __device__ __forceinline__ void batch_producer(const BatchArgs &a, uint8_t *sBuf
       uint32_t t = 0;
       if (lane == 0) {
         t = next_chunk;
-        if (t < a.n_items) next_chunk = atomicAdd(a.ticket, kBatchChunk);
+        if (t < a.n_items) next_chunk = atomicAdd(a.ticket, a.chunk);
       }
       item = __shfl_sync(0xFFFFFFFFu, t, 0);
-      left = kBatchChunk;
+      left = a.chunk;
     } else {
       ++item;
     }
@@ -580,6 +588,7 @@ __global__ void __launch_bounds__(THREADS + 32, batch_min_blocks<THREADS, MAXSB>
   uint32_t *const sMisc = reinterpret_cast<uint32_t *>(empty + R);  // split-run counters, starts, ...
   uint32_t *const s_warp = sMisc + 16;                              // 33 words
   const uint32_t tid = threadIdx.x;
+  if (tid < THREADS) partition_selectors<THREADS>(sMisc + kBatchPermWord);
   if (tid == 0) {
     for (uint32_t i = 0; i < R; ++i) {
       mbar_init(&full[i], 1);
@@ -801,7 +810,9 @@ inline cudaError_t batch_launch(const BatchArgs &a, uint32_t threads, uint32_t m
     occ = std::max(occ, 1);
     if (ctas_per_sm) occ = std::min<int>(occ, (int)ctas_per_sm);
     const int grid = (int)std::min<uint64_t>((uint64_t)occ * sms, std::max<uint32_t>(a.n_items, 1));
-    kern<<<grid, th + 32, sm, st>>>(a);
+    BatchArgs b = a;
+    b.chunk = std::max<uint32_t>(1, std::min<uint32_t>(kBatchChunk, a.n_items / (8u * (uint32_t)grid)));
+    kern<<<grid, th + 32, sm, st>>>(b);
     return cudaGetLastError();
   };
   if (threads == 128) {

@@ -675,7 +675,7 @@ constexpr uint32_t split_smem_bytes() {
   // ones-prefix}, two sets (tile parity) of per-warp {ones, prefix share},
   // the level table, mbarriers, tickets, run counters and run starts
   return DEPTH * 32u * WPT * THREADS * SB + (THREADS / 32) * stage_bytes<SB, WPT>() + 8u * WPT * THREADS +
-         16u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 192u;
+         16u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 192u + (SB == 1 ? 1024u : 0u);
 }
 
 // Phase C of a warp whose symbols span several nodes (the tile is not in
@@ -894,7 +894,25 @@ struct SplitShared {
   uint32_t *cnt;   // 4 run counters
   uint32_t *run;   // 2 run starts
   uint32_t *nc;    // node-count cache of thread 0: {node, ones of child 2 node, of child 2 node + 1}
+  const uint32_t *perm = nullptr;  // 1-byte symbols: the 256 partition selectors (partition_selectors)
 };
+
+// Selectors of the stable partition of 8 bytes by an 8-bit mask m (bit j set:
+// byte j is a one): the bytes whose bit is clear, in order, then those whose
+// bit is set, in order.  Entry m holds two byte-permute selectors (output
+// bytes 0-3 in its low half, 4-7 in its high half), each a nibble per output
+// byte naming the source byte 0..7 of the pair (low word, high word).
+// Filled by threads 0..THREADS-1.
+template <int THREADS>
+__device__ __forceinline__ void partition_selectors(uint32_t *perm) {
+  for (uint32_t m = threadIdx.x; m < 256; m += THREADS) {
+    uint32_t sel = 0, o = 0;
+    for (uint32_t side = 0; side < 2; ++side)
+      for (uint32_t j = 0; j < 8; ++j)
+        if (((m >> j) & 1u) == side) sel |= j << (4 * o++);
+    perm[m] = sel;
+  }
+}
 
 // Per-thread results of pass A that the rest of the tile uses.
 template <int WPT>
@@ -1071,7 +1089,36 @@ __device__ __forceinline__ uint32_t split_tile_rest(const SplitArgs &a, const ui
       const uint8_t *segIn = sIn + seg * SB;
       Sym *const zS = reinterpret_cast<Sym *>(stage + zoff);
       Sym *const oS = reinterpret_cast<Sym *>(stage + ooff);
-      if (nvw == SPW) {
+      if (SB == 1 && sm.perm && nvw == SPW) {
+        // 1-byte symbols: the lane partitions its 8 symbols in registers
+        // (two byte permutes, selectors by the 8-bit pattern), so that its
+        // zeros are bytes 0..nz-1 and its ones bytes nz..7, then stores
+        // byte i at the zero pointer + i or the one pointer + i - nz: one
+        // select and one store per symbol, no pointer updates.
+        const uint32_t zbase = smem_addr(zS), obase = smem_addr(oS);
+        const uint32_t mbyte = 0x4440u | (lane & 3u);  // byte-permute selector of byte lane % 4
+#pragma unroll
+        for (uint32_t s = 0; s < 32 * WPT / 8; ++s) {
+          const uint32_t pos0 = 256 * s + 8 * lane;
+          const uint2 wp = sWP[32 * WPT * warp + 8 * s + wsub];
+          const uint2 grp = *reinterpret_cast<const uint2 *>(segIn + pos0);
+          const uint32_t m = __byte_perm(wp.x, 0u, mbyte);    // the bits of the lane's 8 symbols
+          const uint32_t sel = sm.perm[m];
+          const uint32_t lo = __byte_perm(grp.x, grp.y, sel & 0xFFFFu);
+          const uint32_t hi = __byte_perm(grp.x, grp.y, sel >> 16);
+          const uint32_t nz = 8u - __popc(m);
+          const uint32_t zm = (1u << nz) - 1u;                 // bit i set: byte i is a zero
+          const uint32_t Rl = wp.y + __popc(wp.x & lowmask);  // ones before pos0 in the warp
+          const uint32_t za = zbase + (pos0 - Rl);             // byte i < nz goes to za + i
+          const uint32_t ob = obase + Rl - nz;                 // byte i >= nz goes to ob + i
+#pragma unroll
+          for (uint32_t i = 0; i < 8; ++i) {
+            const uint32_t v = (i < 4 ? lo : hi) >> (8 * (i & 3));
+            const uint32_t addr = ((zm & (1u << i)) ? za : ob) + i;
+            asm volatile("st.shared.u8 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+          }
+        }
+      } else if (nvw == SPW) {
         // Each symbol goes to the running zero or one pointer of its lane:
         // one predicate, two predicated stores, two predicated increments --
         // no branch, whatever the bits.
@@ -1225,6 +1272,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
   uint32_t *const sCnt = pipe.ring + 4;              // 2 x 4 run counters
   uint32_t *const sRun = sCnt + 8;                   // 2 x 2 run starts
   uint32_t *const sNc = sRun + 4;                    // node-count cache (3 words)
+  uint32_t *const sPerm = sNc + 16;                  // 1-byte symbols: partition selectors
   pipe.in = a.in;
   pipe.in_padded = a.in_padded;
   pipe.n = a.n;
@@ -1251,6 +1299,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
     for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
   }
   if (tid < 8) sCnt[tid] = 0;
+  if (SB == 1) partition_selectors<THREADS>(sPerm);
   if (tid == 0) {
     sNc[0] = 0xFFFFFFFFu;
     pipe.prologue();
@@ -1282,7 +1331,8 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
       uint8_t *const sIn = pipe.data(it);
       if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
       const uint32_t par = it & 1u;
-      const SplitShared sm{sStage, sWP, sWT + par * NW, sCnt + 4 * par, sRun + 2 * par, sNc};
+      const SplitShared sm{sStage, sWP, sWT + par * NW, sCnt + 4 * par, sRun + 2 * par, sNc,
+                           SB == 1 ? sPerm : nullptr};
       const SplitPassA<WPT> pa = split_pass_a<SB, THREADS, WPT>(a, sIn, nv, pre.sum(), sWP, sm.wt);
       if (tid == 0) pipe.ring[(it + 2) % 3] = nn;
       if (__syncthreads_or(!ok)) {
@@ -1322,7 +1372,7 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
       uint8_t *const sIn = pipe.data(it);
       if (pipe.fill_tail(sIn, start, nv)) __syncthreads();
 
-      const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc};
+      const SplitShared sm{sStage, sWP, sWT, sCnt, sRun, sNc, SB == 1 ? sPerm : nullptr};
       split_tile<SB, THREADS, NC, WPT>(a, tab, tile, sIn, pre.sum(), sm,
                                        tid == 0 ? &pipe.ring[(it + 2) % 3] : nullptr, nn);
       if (tid == 0) pipe.after_tile(nxt);
