@@ -208,12 +208,56 @@ __device__ __forceinline__ void load_from_smem(const uint8_t *sIn, uint32_t my0,
 // thread that owns it; per-thread 16-byte loads of 64 or 128 consecutive
 // bytes would serialise 4 or 8 ways on the shared-memory banks.
 // Called by all threads of the warp.
+// Bit k of the 32 * WPT consecutive 1-byte symbols at my0 (WPT words).  The
+// thread reads its 2 * WPT 16-byte chunks in an order rotated by lane: the
+// eight lanes of a quarter-warp, whose chunks lie 32 * WPT bytes apart,
+// would otherwise meet in 2 (WPT = 1) or 4 (WPT = 2) of the eight 16-byte
+// bank groups on every load; rotated, each load of the quarter-warp touches
+// all eight once.  The packed bits are rotated back into place.
+template <int WPT>
+__device__ __forceinline__ void tile_words_1b(const uint8_t *sIn, uint32_t my0, uint32_t k, uint32_t (&w)[WPT]) {
+  static_assert(WPT == 1 || WPT == 2, "one or two words per thread");
+  constexpr uint32_t NC = 2 * WPT;                    // 16-byte chunks of the thread
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t r = (lane / (8 / NC)) & (NC - 1);    // rotation of the chunk order
+  const uint4 *src = reinterpret_cast<const uint4 *>(sIn + my0);
+  uint32_t p[NC];
+#pragma unroll
+  for (uint32_t j = 0; j < NC; ++j) {
+    const uint4 v = src[(j + r) & (NC - 1)];
+    const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+    uint32_t bits = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      // bit k of each byte to bit 0 of the byte, then gather the four bits
+      // into the top nibble with one multiply (no carries between terms)
+      const uint32_t x = (q[m] >> k) & 0x01010101u;
+      bits |= ((x * 0x10204080u) >> 28) << (4 * m);
+    }
+    p[j] = bits;  // 16 bits: chunk (j + r) mod NC
+  }
+  if constexpr (WPT == 1) {
+    w[0] = __funnelshift_l(p[0] | (p[1] << 16), p[0] | (p[1] << 16), 16 * r);  // rotate left by 16 r
+  } else {
+    // the 64-bit value with chunk (j + r) mod 4 at bits 16 j, rotated left by 16 r
+    uint32_t lo = p[0] | (p[1] << 16), hi = p[2] | (p[3] << 16);
+    if (r & 2u) {
+      const uint32_t t = lo;
+      lo = hi;
+      hi = t;
+    }
+    const uint32_t sh = 16u * (r & 1u);
+    w[0] = __funnelshift_l(hi, lo, sh);
+    w[1] = __funnelshift_l(lo, hi, sh);
+  }
+}
+
 template <int SB, int THREADS>
 __device__ __forceinline__ uint32_t tile_word(const uint8_t *sIn, uint32_t my0, uint32_t k) {
   if (SB == 1) {
-    uint32_t u[8];
-    load_from_smem<1, THREADS>(sIn, my0, u);
-    return pack_bits<1>(u, k);
+    uint32_t w[1];
+    tile_words_1b<1>(sIn, my0, k, w);
+    return w[0];
   } else {
     using Sym = typename SymT<SB>::type;
     const uint32_t lane = threadIdx.x & 31;
@@ -934,10 +978,19 @@ __device__ __forceinline__ SplitPassA<WPT> split_pass_a(const SplitArgs &a, cons
   const uint32_t my0 = 32 * WPT * tid;
   SplitPassA<WPT> r;
   uint32_t pc = 0;
+  if constexpr (SB == 1) {
+    tile_words_1b<WPT>(sIn, my0, k, r.word);
 #pragma unroll
-  for (int i = 0; i < WPT; ++i) {
-    r.word[i] = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k) & valid_mask(my0 + 32 * i, nv);
-    pc += __popc(r.word[i]);
+    for (int i = 0; i < WPT; ++i) {
+      r.word[i] &= valid_mask(my0 + 32 * i, nv);
+      pc += __popc(r.word[i]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < WPT; ++i) {
+      r.word[i] = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k) & valid_mask(my0 + 32 * i, nv);
+      pc += __popc(r.word[i]);
+    }
   }
   uint32_t incl = pc;
 #pragma unroll
@@ -1573,10 +1626,17 @@ __global__ void __launch_bounds__(THREADS, lastpair_min_blocks<SB, THREADS, WPT>
     {
       unsigned long long zacc = 0, oacc = 0;
       uint32_t zf = 0, of = 0;
+      uint32_t w1s[WPT];  // the thread's level-(L-1) bit words
+      if constexpr (SB == 1) {
+        tile_words_1b<WPT>(sIn, my0, k1, w1s);
+      } else {
+#pragma unroll
+        for (int i = 0; i < WPT; ++i) w1s[i] = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k1);
+      }
 #pragma unroll
       for (int i = 0; i < WPT; ++i) {
         const uint32_t vm = valid_mask(my0 + 32 * i, nv);
-        const uint32_t w1 = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k1) & vm;
+        const uint32_t w1 = w1s[i] & vm;
         const uint32_t w0 = pa.word[i];
 #pragma unroll
         for (uint32_t g = 0; g < 8; ++g) {
