@@ -28,8 +28,7 @@ struct BTree {
   // of each level counts, per child node, the next level's ones into `hist`,
   // and a node-table phase turns them into that level's tables
   uint32_t nc;
-  uint32_t chunk_shift;     // node-table and leaf-start items cover 2^chunk_shift nodes
-  unsigned long long *status;  // look-back words of the node-table phases (cleared per build)
+  uint32_t chunk_shift;     // node-table chunks and leaf-start items cover 2^chunk_shift nodes
 };
 
 // What a phase of a tree does, and on which level.
@@ -62,7 +61,7 @@ __host__ __device__ __forceinline__ uint32_t batch_phase_items(uint32_t nc, uint
                                                               uint32_t chunk_shift, uint32_t ph) {
   const PhaseInfo pi = batch_phase(nc, L, ph);
   if (pi.kind == kPhTables) return 1u;
-  if (pi.kind == kPhNodeTables) return (((1u << pi.level) - 1u) >> chunk_shift) + 1u;
+  if (pi.kind == kPhNodeTables) return 1u;
   if (pi.kind == kPhLeafStarts) return (((1u << (L - 1)) - 1u) >> chunk_shift) + 1u;
   return NT;
 }
@@ -269,16 +268,19 @@ __device__ void batch_tile(const BTree &tr, PhaseInfo pi, uint32_t tile, uint32_
   }
 }
 
-// Node tables of level m of a node-count tree, for the nodes of chunk
-// `chunk` (2^chunk_shift nodes, 8 per thread): the same tables as the
-// single-tree build's node-table kernel, with the scan across chunks by
-// look-back over the tree's status words of the level.  With s(q) = start
-// of node q and c(q) its ones: O_m(q) = sum of c over nodes < q, tab_m[q] =
-// {O_m(q), s(q+1) - c(q) - O_m(q)}; an odd node starts where its parent's
-// 1-child does, an even node where its parent does (written before).
+// Node tables of level m of a node-count tree: the same tables as the
+// single-tree build's node-table kernel, by one block, chunk by chunk
+// (2^chunk_shift nodes, 8 per thread), the scan carried from chunk to
+// chunk.  With s(q) = start of node q and c(q) its ones: O_m(q) = sum of c
+// over nodes < q, tab_m[q] = {O_m(q), s(q+1) - c(q) - O_m(q)}; an odd node
+// starts where its parent's 1-child does, an even node where its parent
+// does (written before).  One item per level: chunks scanned by several
+// blocks through a look-back each waited for a chunk that sat in another
+// block's queue behind another tree's waiting chunk, and those waits
+// chained from block to block (levels 12-14 of a 512-tree batch took 4, 8
+// and 15 ms).
 template <int THREADS>
-__device__ void batch_node_tables(const BTree &tr, uint32_t m, uint32_t chunk, uint32_t *s_warp,
-                                  uint32_t spin_limit) {
+__device__ void batch_node_tables(const BTree &tr, uint32_t m, uint32_t *s_warp) {
   constexpr uint32_t ITEMS = 8;
   const uint32_t tid = threadIdx.x;
   const uint32_t cnt = 1u << m, sh = tr.L - m;
@@ -286,7 +288,6 @@ __device__ void batch_node_tables(const BTree &tr, uint32_t m, uint32_t chunk, u
   const uint2 *tab_prev = tr.tab + ((cnt >> 1) - 1);
   uint2 *tab = tr.tab + (cnt - 1);
   unsigned long long *E = tr.node_start;
-  const uint32_t base = (chunk << tr.chunk_shift) + tid * ITEMS;
   auto start_of = [&](uint32_t q) -> uint32_t {  // s(q), 0 <= q <= 2^m
     if (q >= cnt) return tr.n;
     if (q & 1u) {
@@ -295,40 +296,32 @@ __device__ void batch_node_tables(const BTree &tr, uint32_t m, uint32_t chunk, u
     }
     return (uint32_t)E[(uint64_t)q << sh];
   };
-  uint32_t c[ITEMS];
-  uint32_t sum = 0;
+  uint32_t carry = 0;  // ones of the nodes of the chunks before
+  for (uint32_t base0 = 0; base0 < cnt; base0 += 1u << tr.chunk_shift) {
+    const uint32_t base = base0 + tid * ITEMS;
+    uint32_t c[ITEMS];
+    uint32_t sum = 0;
 #pragma unroll
-  for (uint32_t i = 0; i < ITEMS; ++i) {
-    c[i] = base + i < cnt ? __ldcg(&ones[base + i]) : 0u;
-    sum += c[i];
-  }
-  uint32_t total;
-  const uint32_t excl = block_exclusive_scan<THREADS>(sum, s_warp, &total);
-  // the level's look-back words follow those of the levels before it
-  uint32_t first = 0;
-  for (uint32_t l = 1; l < m; ++l) first += (((1u << l) - 1u) >> tr.chunk_shift) + 1u;
-  if (tid < 32) {
-    Lookback lb;
-    lb.status = tr.status + first;
-    lb.epoch = 1;  // the words are cleared before every build
-    lb.spin_limit = spin_limit;
-    lb.skip = 0;
-    lb.err = tr.err;
-    const uint32_t P = lookback(lb, chunk, 0, total);
-    if (tid == 0) s_warp[32] = P;
-  }
-  cta_sync<THREADS>();
-  uint32_t O = s_warp[32] + excl;
-#pragma unroll
-  for (uint32_t i = 0; i < ITEMS; ++i) {
-    const uint32_t q = base + i;
-    if (q < cnt) {
-      if (q & 1u) E[(uint64_t)q << sh] = start_of(q);
-      tab[q] = make_uint2(O, start_of(q + 1) - c[i] - O);
+    for (uint32_t i = 0; i < ITEMS; ++i) {
+      c[i] = base + i < cnt ? __ldcg(&ones[base + i]) : 0u;
+      sum += c[i];
     }
-    O += c[i];
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan<THREADS>(sum, s_warp, &total);
+    uint32_t O = carry + excl;
+#pragma unroll
+    for (uint32_t i = 0; i < ITEMS; ++i) {
+      const uint32_t q = base + i;
+      if (q < cnt) {
+        if (q & 1u) E[(uint64_t)q << sh] = start_of(q);
+        tab[q] = make_uint2(O, start_of(q + 1) - c[i] - O);
+      }
+      O += c[i];
+    }
+    carry += total;
+    cta_sync<THREADS>();  // s_warp is reused by the next chunk's scan
   }
-  if (m == 1 && chunk == 0 && tid == 0) {
+  if (m == 1 && tid == 0) {
     E[0] = 0;
     E[1ull << tr.L] = tr.n;
   }
@@ -620,7 +613,7 @@ __global__ void __launch_bounds__(THREADS + 32, batch_min_blocks<THREADS, MAXSB>
       if (pi.kind == kPhTables) {
         tables_one_cta<THREADS>(tr.hist, tr.L, tr.node_start, tr.tab, s_warp);
       } else if (pi.kind == kPhNodeTables) {
-        batch_node_tables<THREADS>(tr, pi.level, tile, s_warp, a.spin_limit);
+        batch_node_tables<THREADS>(tr, pi.level, s_warp);
       } else if (pi.kind == kPhLeafStarts) {
         batch_leaf_starts<THREADS>(tr, tile);
       } else {
@@ -664,8 +657,7 @@ struct BatchGeo {
   uint64_t bits, rank, zeros, ns, tab, buf, ctrl;
   uint32_t L, phases;
   bool nc;               // node counts instead of a histogram
-  uint32_t chunk_shift;  // nodes per node-table item: 2^chunk_shift
-  uint64_t status;       // look-back words of the node-table phases
+  uint32_t chunk_shift;  // nodes per node-table chunk and leaf-start item: 2^chunk_shift
 };
 
 inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -701,13 +693,10 @@ inline bool batch_geo(const wt_seq_desc &d, uint32_t threads, BatchGeo &g) {
   g.nc = g.L >= 2 && g.nbins > kBatchHistSmem;
   g.chunk_shift = 0;
   while ((1u << g.chunk_shift) < 8u * threads) ++g.chunk_shift;  // 8 nodes per consumer thread
-  g.status = 0;
-  if (g.nc)
-    for (uint32_t l = 1; l + 1 < g.L; ++l) g.status += (((1ull << l) - 1) >> g.chunk_shift) + 1;
   g.phases = g.nc ? 2 * g.L : (g.L >= 1 ? g.L + 2 : 2);
   // control block: error word, histogram (or node counts), tile counts,
-  // phase counters, stamp, look-back words of the node-table phases
-  g.ctrl = al256((1 + g.nbins + Lz * g.cpl + g.phases) * 4 + 16 + 8 * g.status + 8);
+  // phase counters, stamp
+  g.ctrl = al256((1 + g.nbins + Lz * g.cpl + g.phases) * 4 + 16 + 8);
   return true;
 }
 
@@ -743,7 +732,6 @@ inline BTree batch_tree(const wt_seq_desc &d, const BatchGeo &g, unsigned char *
   t.phases = g.phases;
   t.t_done = reinterpret_cast<unsigned long long *>(
       (reinterpret_cast<uintptr_t>(t.done + g.phases) + 7) & ~uintptr_t(7));
-  t.status = t.t_done + 1;
   t.nc = g.nc ? 1u : 0u;
   t.chunk_shift = g.chunk_shift;
   t.n = (uint32_t)g.n;
