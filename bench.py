@@ -880,13 +880,19 @@ def tree_algorithmic_bytes(n: int, sigma: int, b: int) -> float:
             + algorithmic_bytes("leaf", L - 1, n, b, L))
 
 
-def run_batch(dev, m: int, seed: int, threads: int, steps: int, warmup: int, with_cpu: bool, host_seqs=None):
+def run_batch(dev, m: int, seed: int, threads: int, steps: int, warmup: int, with_cpu: bool, host_seqs=None,
+              recipe: str = "config4"):
     """Config 4: m sequences built in one persistent launch captured in a CUDA
     graph, versus one plain build per sequence, back to back on one stream.
-    Returns the measurements as a dict."""
+    recipe "config1": m independent config-1 sequences (n = 2^20 uint8,
+    uniform over sigma = 256, seeds seed + i) instead.  Returns the
+    measurements as a dict."""
     import torch
     from paper_1407_8142_gb300 import autotune, synth, wt
-    specs4 = synth.config4_specs(m, seed=seed)
+    if recipe == "config1":
+        specs4 = [(1 << 20, 256, 1, seed + i) for i in range(m)]
+    else:
+        specs4 = synth.config4_specs(m, seed=seed)
     specs = [(n, sg, b) for n, sg, b, _ in specs4]
     t0 = time.perf_counter()
     host, seqs = gen_batch_inputs(specs4, dev)
@@ -950,9 +956,12 @@ def run_batch(dev, m: int, seed: int, threads: int, steps: int, warmup: int, wit
     alg = sum(tree_algorithmic_bytes(n, sg, b) for n, sg, b in specs)
     peak, peak_kind = measured_hbm_peak()
     gbs = alg / (ms_batch * 1e-3) / 1e9
-    return {"workload": "batched build: %d sequences, lengths floor(2^U(10,22)), sigma in {4, 256, 65536} "
-                        "(uint8/uint8/uint16), uniform symbols, seed %d; one persistent launch in a CUDA graph"
-                        % (m, seed),
+    workload = ("batched build: %d sequences, lengths floor(2^U(10,22)), sigma in {4, 256, 65536} "
+                "(uint8/uint8/uint16), uniform symbols, seed %d; one persistent launch in a CUDA graph" % (m, seed))
+    if recipe == "config1":
+        workload = ("batched build: %d config-1 sequences (n = 2^20 uint8, uniform over sigma = 256, seeds "
+                    "%d..%d); one persistent launch in a CUDA graph" % (m, seed, seed + m - 1))
+    return {"workload": workload,
             "sequences": m, "total_symbols": total, "tile_threads": threads, "generate_s": round(t_gen, 1),
             "batched": {"ms": ms_batch, "symbols_per_s": total / (ms_batch * 1e-3),
                         "latency_ms_p50": float(np.percentile(lat_b, 50)),
@@ -978,12 +987,12 @@ def main_batch(args):
     import __graft_entry__
     __graft_entry__.build()
     r = run_batch(dev, args.batch_m, args.seed, args.tile_threads, max(args.steps // 10, 3), args.warmup,
-                  not args.no_cpu_baseline)
+                  not args.no_cpu_baseline, recipe=args.batch_recipe)
     ms = r["batched"]["ms"]
     line = {"metric": "batched levelWT: input symbols/s over %d sequences" % args.batch_m,
             "value": r["batched"]["symbols_per_s"], "unit": UNIT, "n_gpus": 1, "steps": r["batched"]["steps"],
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
+            "vs_baseline": None, "dtype": "u8" if args.batch_recipe == "config1" else "u8/u16", "data": "synthetic",
             "config": {"workload": r["workload"], "sequences": r["sequences"], "total_symbols": r["total_symbols"],
                        "tile_threads": r["tile_threads"], "generate_s": r["generate_s"]},
             "batched": r["batched"], "plain": r["plain"], "speedup": r["speedup"], "roofline": r["roofline"],
@@ -1287,6 +1296,8 @@ def main(argv=None):
                          "build; serve: the request-serving trace; query: batched access/rank/select")
     ap.add_argument("--query-m", type=int, default=1 << 24, help="queries per batch (query workload)")
     ap.add_argument("--batch-m", type=int, default=4096)
+    ap.add_argument("--batch-recipe", choices=["config4", "config1"], default="config4",
+                    help="batch workload: the config-4 mix, or m copies of the config-1 recipe")
     ap.add_argument("--serve-horizon", type=float, default=10.0)
     ap.add_argument("--serve-inflight", type=int, default=4)
     ap.add_argument("--serve-plain-cap", type=float, default=60.0,
