@@ -333,6 +333,11 @@ __device__ void batch_node_tables(const BTree &tr, uint32_t m, uint32_t *s_warp)
 // s(q+1) - c(q).  Also E[0] = 0 and E[2^L] = n.
 template <int THREADS>
 __device__ void batch_leaf_starts(const BTree &tr, uint32_t chunk) {
+  // Every node's inputs were written by earlier phases, so a thread issues
+  // the loads of G nodes before it uses any of them (node by node, each
+  // node's loads waited for the previous node's stores: 37 us per item of
+  // 1024 nodes in a config-4 batch).
+  constexpr uint32_t G = THREADS >= 256 ? 2 : 1;  // nodes per thread whose loads are in flight together (registers)
   const uint32_t L = tr.L;
   const uint32_t cnt = 1u << (L - 1);
   const uint32_t *ones = tr.hist + (cnt - 1);
@@ -340,24 +345,32 @@ __device__ void batch_leaf_starts(const BTree &tr, uint32_t chunk) {
   unsigned long long *E = tr.node_start;
   const uint32_t q0 = chunk << tr.chunk_shift;
   const uint32_t q1 = min(cnt, q0 + (1u << tr.chunk_shift));
-  for (uint32_t q = q0 + threadIdx.x; q < q1; q += THREADS) {
-    uint32_t next;
-    if (q + 1 >= cnt) {
-      next = tr.n;
-    } else if ((q + 1) & 1u) {
-      const uint2 t = tab_prev[(q + 1) >> 1];
-      next = t.x + t.y;
-    } else {
-      next = (uint32_t)E[2ull * (q + 1)];
+  for (uint32_t qb = q0 + threadIdx.x; qb < q1; qb += G * THREADS) {
+    uint2 tp[G];
+    uint32_t c1[G];
+    uint32_t en[G];
+#pragma unroll
+    for (uint32_t i = 0; i < G; ++i) {
+      const uint32_t q = qb + i * THREADS;
+      if (q < q1) {
+        tp[i] = tab_prev[q >> 1];  // q odd: its own start; q even: its 1-sibling's, where q ends
+        c1[i] = __ldcg(&ones[q]);
+        en[i] = ((q & 1u) && q + 1 < cnt) ? (uint32_t)E[2ull * (q + 1)] : 0u;  // an even node's start
+      }
     }
-    if (q & 1u) {
-      const uint2 t = tab_prev[q >> 1];
-      E[2ull * q] = t.x + t.y;
-    }
-    E[2ull * q + 1] = next - __ldcg(&ones[q]);
-    if (q == 0) {
-      E[0] = 0;
-      E[1ull << L] = tr.n;
+#pragma unroll
+    for (uint32_t i = 0; i < G; ++i) {
+      const uint32_t q = qb + i * THREADS;
+      if (q < q1) {
+        const uint32_t sib = tp[i].x + tp[i].y;
+        const uint32_t next = q + 1 >= cnt ? tr.n : (q & 1u) ? en[i] : sib;
+        if (q & 1u) E[2ull * q] = sib;
+        E[2ull * q + 1] = next - c1[i];
+        if (q == 0) {
+          E[0] = 0;
+          E[1ull << L] = tr.n;
+        }
+      }
     }
   }
 }
