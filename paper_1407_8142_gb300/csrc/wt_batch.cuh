@@ -217,6 +217,10 @@ __device__ void batch_tile(const BTree &tr, PhaseInfo pi, uint32_t tile, uint32_
     a.count_table = 0;
     a.tab_out = nullptr;
     a.nones_next = tr.nc ? tr.hist + ((2u << level) - 1) : nullptr;
+    a.node_ones = nullptr;  // the level's table comes from its node-table phase
+    a.tab_prev = nullptr;
+    a.tab_w = nullptr;
+    a.E = nullptr;
     a.lo = lo;
     a.cin = tree_counts(tr, level);
     a.cout = tree_counts(tr, level + 1);

@@ -206,6 +206,28 @@ int launch_leaf(Launcher &ln, const uint8_t *in, bool in_padded, uint32_t level)
   return WT_OK;
 }
 
+// Whether the pass over `level` computes that level's node table itself
+// (SplitArgs::node_ones): node counts, one level per pass, and at most one
+// node per thread of the pass's CTA with the table in shared memory (CTA
+// and table sizes as chosen by launch_split and launch_lastpair); the
+// node-table kernel of the level is then not launched.
+bool tables_in_pass(const wt_tree *t, uint32_t level) {
+  if (!t->node_counts || t->fuse_k != 1 || level == 0) return false;
+  const uint32_t cta = (t->sb == 1 && t->threads == 512) ? 256u : t->threads;
+  const uint32_t smem_nodes = t->sb == 1 ? 128u : 1024u;
+  return (1ull << level) <= std::min(cta, smem_nodes);
+}
+
+// Set the node-table fields of a pass's arguments (none if the level's
+// table comes from the node-table kernel or the level has one node).
+void set_pass_tables(const wt_tree *t, uint32_t level, SplitArgs &a) {
+  const bool own = tables_in_pass(t, level);
+  a.node_ones = own ? t->d_hist + ((1u << level) - 1) : nullptr;
+  a.tab_prev = own ? t->d_tab + ((1u << (level - 1)) - 1) : nullptr;
+  a.tab_w = own ? t->d_tab + ((1u << level) - 1) : nullptr;
+  a.E = own ? t->d_node_start : nullptr;
+}
+
 template <int SB, int THREADS>
 int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, uint32_t level) {
   wt_tree *t = ln.t;
@@ -229,6 +251,7 @@ int launch_split(Launcher &ln, const uint8_t *in, bool in_padded, uint8_t *out, 
   a.count_table = count_table ? 1 : 0;
   a.tab_out = (t->node_counts && level == 0) ? t->d_tab : nullptr;
   a.nones_next = t->node_counts ? t->d_hist + ((2u << level) - 1) : nullptr;
+  set_pass_tables(t, level, a);
   a.lo = ln.out(level);
   a.cin = ln.counts(level);
   a.cout = ln.counts(level + 1);
@@ -278,6 +301,7 @@ int launch_lastpair(Launcher &ln, const uint8_t *in, bool in_padded) {
   a.count_table = count_table ? 1 : 0;
   a.tab_out = (t->node_counts && level == 0) ? t->d_tab : nullptr;
   a.nones_next = t->node_counts ? t->d_hist + ((2u << level) - 1) : nullptr;
+  set_pass_tables(t, level, a);
   a.lo = ln.out(level);
   a.cin = ln.counts(level);
   a.cout = ln.counts(level);  // unused: no T_{L-1}
@@ -458,7 +482,7 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
   const uint32_t last_split = pair ? t->L - 2 : t->L - 1;  // levels below it take one split pass each
   for (uint32_t l = 0; l < last_split; ++l) {
     // with node counts, the tables of level l come from the pass over l-1
-    if (t->node_counts && l >= 1 && (rc = launch_node_tables(ln, l))) return rc;
+    if (t->node_counts && l >= 1 && !tables_in_pass(t, l) && (rc = launch_node_tables(ln, l))) return rc;
     uint8_t *out = static_cast<uint8_t *>(t->d_buf[l & 1]);
     if ((rc = launch_split<SB, THREADS>(ln, in, padded, out, l))) return rc;
     if (t->record_levels) WT_CUDA(cudaEventRecord(t->level_ev[l], st));  // level l's rows are final
@@ -467,7 +491,7 @@ int run_build(wt_tree *t, const uint8_t *seq, bool seq_padded, cudaStream_t st) 
   }
   if (pair) {
     const uint32_t m = t->L - 2;
-    if (t->node_counts && m >= 1 && (rc = launch_node_tables(ln, m))) return rc;
+    if (t->node_counts && m >= 1 && !tables_in_pass(t, m) && (rc = launch_node_tables(ln, m))) return rc;
     if ((rc = launch_lastpair<SB, THREADS>(ln, in, padded))) return rc;
     if (t->record_levels) WT_CUDA(cudaEventRecord(t->level_ev[m], st));
     if (t->node_counts && (rc = launch_node_tables(ln, t->L - 1))) return rc;
@@ -934,7 +958,11 @@ int wt_kernels_per_build(const wt_tree *t) {
     return k;
   }
   int k = 1;                                              // pre-pass
-  if (t->node_counts) k += (int)t->L - 1;                 // node tables, levels 1..L-1
+  if (t->node_counts) {  // node tables of levels 1..L-2 (unless the pass over the level makes
+                         // its own) and the node starts of the last level
+    for (uint32_t l = 1; l + 1 < t->L; ++l) k += tables_in_pass(t, l) ? 0 : 1;
+    k += 1;
+  }
   else if (t->shape == WT_SHAPE_TREE) k += 1 + (tables_blocks(t->L) ? 1 : 0);  // histogram scan, tables
   if (t->L >= 1) k += (int)(t->L - 1) + 1;    // splits + last level
   return k;

@@ -610,6 +610,15 @@ struct SplitArgs {
                        // level's tile counts (wavelet matrix; tree level 0 with node counts)
   uint2 *tab_out;      // if set, CTA 0 also stores that one-node table there
   uint32_t *nones_next;  // if set, ones of level l+1 per child node (2p + bit) are added here
+  // If node_ones is set (node counts, a level of at most one node per
+  // thread), every CTA computes this level's table in shared memory from the
+  // nodes' ones (node_ones), the previous level's table (tab_prev) and the
+  // node starts (E), and CTA 0 also stores it to tab_w and the odd nodes'
+  // starts to E -- what the node-table kernel would have done before the pass.
+  const uint32_t *node_ones;
+  const uint2 *tab_prev;
+  uint2 *tab_w;
+  unsigned long long *E;
   LevelOut lo;
   TileCounts cin;      // ones of level l per tile of T_l
   TileCounts cout;     // ones of level l+1 per tile of T_{l+1} (accumulated here)
@@ -1404,6 +1413,42 @@ constexpr int split_min_blocks() {
   return (int)(r ? r : 1u);
 }
 
+// The level's node table from per-node counts, by one CTA of THREADS
+// threads, node q by thread q (2^level <= THREADS), into sTab; CTA 0 also
+// stores it and the odd nodes' starts (see SplitArgs::node_ones).  With s(q)
+// = start of node q and c(q) its ones: O(q) = sum of c over nodes < q, and
+// tab[q] = {O(q), s(q+1) - c(q) - O(q)}; an odd node starts where its
+// parent's 1-child does, an even node where its parent does (written at an
+// earlier level).  s_warp: 33 words of scratch.  Ends with threads of the
+// CTA still to be synchronised before sTab is read.
+template <int THREADS>
+__device__ __forceinline__ void split_node_table(const SplitArgs &a, uint2 *sTab, uint32_t *s_warp) {
+  const uint32_t q = threadIdx.x, cnt = 1u << a.level, sh = a.L - a.level;
+  auto start_of = [&](uint32_t v) -> uint32_t {
+    if (v >= cnt) return a.n;
+    if (v & 1u) {
+      const uint2 t = a.tab_prev[v >> 1];
+      return t.x + t.y;
+    }
+    return (uint32_t)a.E[(uint64_t)v << sh];
+  };
+  const uint32_t c = q < cnt ? __ldcg(&a.node_ones[q]) : 0u;
+  uint32_t total;
+  const uint32_t O = block_exclusive_scan<THREADS>(c, s_warp, &total);
+  if (q < cnt) {
+    const uint2 tb = make_uint2(O, start_of(q + 1) - c - O);
+    sTab[q] = tb;
+    if (blockIdx.x == 0) {
+      a.tab_w[q] = tb;
+      if (q & 1u) a.E[(uint64_t)q << sh] = start_of(q);
+    }
+  }
+  if (a.level == 1 && blockIdx.x == 0 && q == 0) {
+    a.E[0] = 0;
+    a.E[1ull << a.L] = a.n;
+  }
+}
+
 // NC: the tree's node sizes come from node counts (a.nones_next set): the
 // pass also counts the next level's ones per child node.  Compiled as a
 // separate kernel so that the other builds carry none of that code.
@@ -1447,6 +1492,8 @@ __global__ void __launch_bounds__(THREADS, split_min_blocks<SB, THREADS, DEPTH, 
         if (a.tab_out && blockIdx.x == 0) a.tab_out[0] = sTab[0];
       }
     }
+  } else if (a.node_ones) {
+    split_node_table<THREADS>(a, sTab, reinterpret_cast<uint32_t *>(sStage));
   } else if (tab_smem) {
     for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
   }
@@ -1656,6 +1703,10 @@ __global__ void __launch_bounds__(THREADS, lastpair_min_blocks<SB, THREADS, WPT>
         if (a.tab_out && blockIdx.x == 0) a.tab_out[0] = sTab[0];
       }
     }
+  } else if (a.node_ones) {
+    // scratch: the pass-A words, unused before the barrier below (the
+    // stream areas are cleared before it)
+    split_node_table<THREADS>(a, sTab, reinterpret_cast<uint32_t *>(sWP));
   } else if (tab_smem) {
     for (uint32_t i = tid; i < nodes; i += THREADS) sTab[i] = __ldg(&a.tab[i]);
   }
