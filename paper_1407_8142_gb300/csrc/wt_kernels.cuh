@@ -1615,8 +1615,8 @@ __device__ __forceinline__ void warp_bit_run(const uint32_t *w, uint32_t src, ui
 // the symbol to: within a warp lying in one node, the level-(L-1) bits of
 // its zeros, in order, form one run that starts where its zeros would go,
 // and those of its ones another.  So a thread compacts its words' level-
-// (L-1) bits into those of its zeros and those of its ones (a 256-entry
-// table per 4-bit nibble of value and mask), the warp assembles the two
+// (L-1) bits into those of its zeros and those of its ones (8 at a time, by
+// the byte permutes of the split's stable partition), the warp assembles the two
 // bit streams in shared memory, and writes them as bit runs (the row is
 // zeroed before the pass; each run's end words are or-ed in).  A warp
 // spanning several nodes writes each of its level-(L-1) one bits at its
@@ -1637,9 +1637,10 @@ template <int SB, int THREADS, int WPT = 1>
 constexpr uint32_t lastpair_smem_bytes() {
   // two input tiles, per warp two bit streams (with a zero pad word at each
   // end), per-word {bit word, prefix}, two sets of per-warp {ones, share},
-  // the level table, the nibble table, node counters, mbarriers and tickets
+  // the level table, the partition selectors, node counters, mbarriers and
+  // tickets
   return 2u * 32u * WPT * THREADS * SB + (THREADS / 32) * lastpair_stage_words<SB, WPT>() * 4u +
-         8u * WPT * THREADS + 16u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 256u +
+         8u * WPT * THREADS + 16u * (THREADS / 32) + 8u * tab_smem_nodes<SB>() + 1024u +
          8u * kLastPairSmemNodes + 128u;
 }
 
@@ -1667,8 +1668,8 @@ __global__ void __launch_bounds__(THREADS, lastpair_min_blocks<SB, THREADS, WPT>
   uint2 *const sWP = reinterpret_cast<uint2 *>(sStream + NW * 2 * SW);
   uint2 *const sWT = sWP + WPT * THREADS;         // 2 sets
   uint2 *const sTab = sWT + 2 * NW;
-  uint8_t *const sLut = reinterpret_cast<uint8_t *>(sTab + tab_smem_nodes<SB>());
-  uint32_t *const sNC = reinterpret_cast<uint32_t *>(sLut + 256);  // ones of child 2p + bit at [2p + bit]
+  uint32_t *const sPerm = reinterpret_cast<uint32_t *>(sTab + tab_smem_nodes<SB>());  // partition selectors
+  uint32_t *const sNC = sPerm + 256;  // ones of child 2p + bit at [2p + bit]
   pipe.bar = reinterpret_cast<uint64_t *>(sNC + 2 * kLastPairSmemNodes);
   pipe.ring = reinterpret_cast<uint32_t *>(pipe.bar + 2);
   pipe.in = a.in;
@@ -1683,18 +1684,7 @@ __global__ void __launch_bounds__(THREADS, lastpair_min_blocks<SB, THREADS, WPT>
   const uint32_t k = a.L - 1 - a.level, k1 = k - 1;
   const uint32_t lmask = (1u << a.L) - 1u;
 
-  // nibble table: entry (m << 4) | v holds the bits of v where m is 0,
-  // compacted in order (low nibble), and those where m is 1 (high nibble)
-  for (uint32_t e = tid; e < 256; e += THREADS) {
-    const uint32_t m = e >> 4, v = e & 15u;
-    uint32_t z = 0, o = 0, nz = 0, no = 0;
-    for (uint32_t j = 0; j < 4; ++j) {
-      const uint32_t b = (v >> j) & 1u;
-      if ((m >> j) & 1u) o |= b << no++;
-      else z |= b << nz++;
-    }
-    sLut[e] = (uint8_t)(z | (o << 4));
-  }
+  partition_selectors<THREADS>(sPerm);
   if (a.count_table) {
     if (tid < 32) {
       const uint32_t ones = counts_total_warp(a.cin, a.NT);
@@ -1783,22 +1773,36 @@ __global__ void __launch_bounds__(THREADS, lastpair_min_blocks<SB, THREADS, WPT>
 #pragma unroll
         for (int i = 0; i < WPT; ++i) w1s[i] = tile_word<SB, THREADS>(sIn, my0 + 32 * i, k1);
       }
+      // Per byte (8 symbols): spread the 8 level-(L-1) bits to one per byte
+      // (a multiply and a mask per 4 bits), reorder those bytes with the
+      // stable partition of the split (byte permutes, selectors by the 8
+      // level-(L-2) bits), and gather them back: the zeros' bits, then the
+      // ones', each in order.  Positions past n are neither (their level-
+      // (L-2) bit is 0, so they sort after the valid zeros and are masked off).
 #pragma unroll
       for (int i = 0; i < WPT; ++i) {
         const uint32_t vm = valid_mask(my0 + 32 * i, nv);
-        const uint32_t w1 = w1s[i] & vm;
+        const uint32_t w1 = w1s[i];
         const uint32_t w0 = pa.word[i];
+        uint32_t z32 = 0, o32 = 0, zn = 0, on = 0;  // this word's zeros' and ones' bits
 #pragma unroll
-        for (uint32_t g = 0; g < 8; ++g) {
-          const uint32_t mn = (w0 >> (4 * g)) & 15u, vn = (w1 >> (4 * g)) & 15u;
-          const uint32_t vmn = (vm >> (4 * g)) & 15u;  // positions past n are neither zeros nor ones
-          const uint32_t r = sLut[(mn << 4) | vn];
-          zacc |= (unsigned long long)(r & 15u) << zf;
-          oacc |= (unsigned long long)(r >> 4) << of;
-          const uint32_t c1 = __popc(mn);
-          zf += __popc(vmn) - c1;
-          of += c1;
+        for (uint32_t b = 0; b < 4; ++b) {
+          const uint32_t m = (w0 >> (8 * b)) & 0xFFu, v = (w1 >> (8 * b)) & 0xFFu;
+          const uint32_t sel = sPerm[m];
+          const uint32_t slo = ((v & 15u) * 0x00204081u) & 0x01010101u;  // bit j to byte j
+          const uint32_t shi = ((v >> 4) * 0x00204081u) & 0x01010101u;
+          const uint32_t plo = __byte_perm(slo, shi, sel & 0xFFFFu), phi = __byte_perm(slo, shi, sel >> 16);
+          const uint32_t P = ((plo * 0x10204080u) >> 28) | (((phi * 0x10204080u) >> 28) << 4);  // byte j to bit j
+          const uint32_t c1 = __popc(m), nzv = __popc((vm >> (8 * b)) & 0xFFu) - c1;
+          z32 |= (P & ((1u << nzv) - 1u)) << zn;
+          o32 |= (P >> (8u - c1)) << on;
+          zn += nzv;
+          on += c1;
         }
+        zacc |= (unsigned long long)z32 << zf;
+        oacc |= (unsigned long long)o32 << of;
+        zf += zn;
+        of += on;
       }
       // zeros before this thread within the warp: its position in the warp
       // minus the ones before it
