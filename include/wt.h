@@ -134,10 +134,15 @@ int wt_create(uint64_t n, uint32_t sigma, uint32_t symbol_bytes, const wt_config
  * Fig. 1): a pre-pass that histograms the symbols, checks their range and
  * counts level 0's ones per tile, the node tables, one split pass per level
  * l = 0..L-2 (bits, directory and the stable split into T_{l+1}), and a last
- * pass for level L-1 (bits and directory).  For sigma > 2^13 the pre-pass
- * builds no histogram: each split pass counts, per child node, the ones of
- * the next level, and a small kernel before each level turns these counts
- * into that level's node tables and node starts.  With levels_per_pass =
+ * pass for level L-1 (bits and directory).  For sigma > 2^13 and for
+ * n >= 2^24 the pre-pass builds no histogram: each split pass counts, per
+ * child node, the ones of the next level, and these counts become that
+ * level's node tables and node starts -- in the prologue of the pass over
+ * the level when it has at most one node per thread of the pass's blocks,
+ * else in a small kernel before it.  When the nodes of level L-2 average
+ * 2^16 symbols or more, levels L-2 and L-1 are one pass that moves no
+ * symbols (level L-1's bits are compacted straight to their positions),
+ * followed by a directory kernel for level L-1.  With levels_per_pass =
  * k > 1 (see wt_config; the library's choice for 4-byte symbols, at least 8
  * levels and n >= 2^22) each pass builds k levels, after a kernel that
  * counts every tile's k-bit digits (and the node sizes of level l+k, which
