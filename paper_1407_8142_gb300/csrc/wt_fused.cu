@@ -104,22 +104,26 @@ __device__ __forceinline__ uint32_t gran_of(uint32_t h) { return 31u - __clz(h +
 __device__ __forceinline__ uint32_t rev_bits(uint32_t c, uint32_t i) { return i ? __brev(c) >> (32u - i) : 0u; }
 
 // Phase 1 of a round: this warp's V rows of the image into v[] (masked to
-// L bits on the first round), and the ballot of bit `sh` of each row; lane r
-// returns row r's word.  Positions at or past nv read as 0 (bit 0).
-template <typename Sym, uint32_t V, bool FULL>
+// L bits on the first round, MASK), and the ballot of bit `sh` of each row,
+// which lane 0 stores at words[r]; lane r returns row r's word.  Positions
+// at or past nv read as 0 (bit 0).
+template <typename Sym, uint32_t V, bool FULL, bool MASK>
 __device__ __forceinline__ uint32_t round_bits(const Sym *X, uint32_t x0, uint32_t nv, uint32_t sh,
-                                               uint32_t mask, uint32_t (&v)[V]) {
+                                               uint32_t mask, uint32_t *words, uint32_t (&v)[V]) {
+  static_assert(V == 32, "one row word per lane");
   const uint32_t lane = threadIdx.x & 31;
-  uint32_t mine = 0;
+  const uint32_t bm = 1u << sh;
 #pragma unroll
   for (uint32_t r = 0; r < V; ++r) {
     const uint32_t x = x0 + 32 * r;
-    const uint32_t s = (FULL || x < nv) ? ((uint32_t)X[x] & mask) : 0u;
+    uint32_t s = (FULL || x < nv) ? (uint32_t)X[x] : 0u;
+    if (MASK) s &= mask;
     v[r] = s;
-    const uint32_t b = __ballot_sync(0xFFFFFFFFu, (s >> sh) & 1u);
-    if (lane == r) mine = b;
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, (s & bm) != 0u);
+    if (lane == 0) words[r] = b;
   }
-  return mine;
+  __syncwarp();
+  return words[lane];
 }
 
 // Phase 2 of a round: the stable 2-way split of the image in place.  Row r's
@@ -326,10 +330,16 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
 #pragma unroll 1
     for (uint32_t i = 0; i < K; ++i) {
       const uint32_t sh = a.L - 1 - a.level - i;  // bit of level l+i
-      const uint32_t mask = i ? ~0u : lmask;      // later rounds hold masked symbols
-      // ---- phase 1: this round's bit of every symbol, as ballot words
-      const uint32_t mine = full ? round_bits<Sym, V, true>(X, xw + lane, nv, sh, mask, v)
-                                 : round_bits<Sym, V, false>(X, xw + lane, nv, sh, mask, v);
+      // ---- phase 1: this round's bit of every symbol, as ballot words (the
+      // first round masks the symbols to L bits; later rounds hold masked ones)
+      uint32_t *const words = sBits + 1 + warp * V;
+      uint32_t mine;
+      if (i == 0)
+        mine = full ? round_bits<Sym, V, true, true>(X, xw + lane, nv, sh, lmask, words, v)
+                    : round_bits<Sym, V, false, true>(X, xw + lane, nv, sh, lmask, words, v);
+      else
+        mine = full ? round_bits<Sym, V, true, false>(X, xw + lane, nv, sh, lmask, words, v)
+                    : round_bits<Sym, V, false, false>(X, xw + lane, nv, sh, lmask, words, v);
       const uint32_t pc = __popc(mine);
       uint32_t incl = pc;
 #pragma unroll
@@ -337,10 +347,7 @@ __global__ void __launch_bounds__(kFThreads, SB == 4 ? 4 : 3) k_fused(FusedArgs 
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += y;
       }
-      if (lane < V) {
-        sBits[1 + warp * V + lane] = mine;
-        sWP[warp * V + lane] = make_uint2(mine, incl - pc);
-      }
+      sWP[warp * V + lane] = make_uint2(mine, incl - pc);
       if (lane == 31) sWarpOnes[warp] = incl;
       __syncthreads();
 
@@ -604,10 +611,17 @@ struct DirArgs {
 };
 
 // D[b] = ones of the row before bit 512 b, D[NB] = all ones, zeros = n - D[NB];
-// one look-back segment per row.
+// one look-back segment per row.  A CTA takes kScanChunk blocks: thread t
+// counts blocks t, t + kScanThreads, ... (adjacent threads read adjacent
+// 64-byte blocks), the counts are regrouped in shared memory so that thread
+// t scans the kScanItems consecutive blocks from kScanItems t on, and the
+// entries go back out in the loading order.  (Each thread reading its own
+// kScanItems consecutive blocks put the lanes of a load 512 bytes apart.)
 __global__ void __launch_bounds__(kScanThreads) k_dir(DirArgs a) {
+  static_assert(kScanItems == 8, "two 16-byte shared words per thread");
   __shared__ uint32_t s_warp[33];
   __shared__ uint32_t s_tile, s_P;
+  __shared__ __align__(16) uint32_t s_c[kScanChunk];  // counts, then entries minus the chunk's prefix
   const uint32_t tid = threadIdx.x;
   if (tid == 0) s_tile = atomicAdd(a.ticket, 1u);
   __syncthreads();
@@ -615,39 +629,53 @@ __global__ void __launch_bounds__(kScanThreads) k_dir(DirArgs a) {
   if (tile >= a.levels * a.nchunks) return;
   const uint32_t lvl = tile / a.nchunks, chunk = tile - lvl * a.nchunks;
   const uint32_t *rowp = a.bits + (uint64_t)lvl * a.W;
-  const uint32_t b0 = chunk * kScanChunk + tid * kScanItems;
-  uint32_t c[kScanItems];
-  uint32_t sum = 0;
+  const uint32_t cb = chunk * kScanChunk;  // the chunk's first block
 #pragma unroll
   for (uint32_t i = 0; i < kScanItems; ++i) {
-    c[i] = 0;
-    if (b0 + i < a.NB) {
-      const uint4 *p = reinterpret_cast<const uint4 *>(rowp + 16ull * (b0 + i));
+    const uint32_t b = cb + i * kScanThreads + tid;
+    uint32_t c = 0;
+    if (b < a.NB) {
+      const uint4 *p = reinterpret_cast<const uint4 *>(rowp + 16ull * b);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const uint4 w = __ldcg(p + q);
-        c[i] += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+        const uint4 w = __ldg(p + q);
+        c += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
       }
     }
-    sum += c[i];
+    s_c[i * kScanThreads + tid] = c;
   }
+  __syncthreads();
+  uint4 *const s_c4 = reinterpret_cast<uint4 *>(s_c);
+  const uint4 c0 = s_c4[2 * tid], c1 = s_c4[2 * tid + 1];  // blocks cb + 8 tid .. cb + 8 tid + 7
+  const uint32_t sum = c0.x + c0.y + c0.z + c0.w + c1.x + c1.y + c1.z + c1.w;
   uint32_t total;
   const uint32_t excl = block_exclusive_scan<kScanThreads>(sum, s_warp, &total);
   if (tid < 32) {
     const uint32_t P = lookback(a.lb, tile, lvl * a.nchunks, total);
     if (tid == 0) s_P = P;
   }
+  uint4 e0, e1;
+  e0.x = excl;
+  e0.y = e0.x + c0.x;
+  e0.z = e0.y + c0.y;
+  e0.w = e0.z + c0.z;
+  e1.x = e0.w + c0.w;
+  e1.y = e1.x + c1.x;
+  e1.z = e1.y + c1.y;
+  e1.w = e1.z + c1.z;
+  s_c4[2 * tid] = e0;  // this thread's own words: read above by it alone
+  s_c4[2 * tid + 1] = e1;
   __syncthreads();
+  const uint32_t P = s_P;
   unsigned long long *rk = a.rank + (uint64_t)lvl * (a.NB + 1);
-  uint32_t run = s_P + excl;
 #pragma unroll
   for (uint32_t i = 0; i < kScanItems; ++i) {
-    if (b0 + i < a.NB) rk[b0 + i] = run;
-    run += c[i];
+    const uint32_t b = cb + i * kScanThreads + tid;
+    if (b < a.NB) rk[b] = P + s_c[i * kScanThreads + tid];
   }
   if (chunk == a.nchunks - 1 && tid == 0) {
-    rk[a.NB] = s_P + total;
-    a.zeros[lvl] = (unsigned long long)(a.n - (s_P + total));
+    rk[a.NB] = P + total;
+    a.zeros[lvl] = (unsigned long long)(a.n - (P + total));
   }
 }
 
