@@ -39,7 +39,7 @@ ZIPF_S = 1.0
 METRIC = "levelWT build throughput (input symbols/s)"
 MATRIX_METRIC = "wavelet matrix build throughput (input symbols/s)"
 UNIT = "symbols/s"
-CPU_SAMPLE = 1 << 27       # cpu_baseline: first 2^27 symbols of the workload
+CPU_SAMPLE = 1 << 29       # cpu_baseline: first 2^29 symbols of the workload (about 14 s of one host core at config 2)
 E2E_TRIALS = 3  # e2e trials per mode; the median is reported
 REF_STEP_SAMPLE = 1 << 23  # --impl reference: symbols per step
 
