@@ -50,6 +50,19 @@ def pins_pass(o, lib) -> bool:
                          zip(res["node_id"], res["node_start"], res["node_len"])]
                 if nodes != e["nodes"]:
                     return False
+        with open(os.path.join(HERE, "golden", "query_examples.json")) as f:
+            for e in json.load(f)["examples"]:
+                S = np.array(e["S"], dtype=np.uint8)
+                a, r, q = e["access"], e["rank"], e["select"]
+                got = o.access(S, np.array(a["i"], dtype=np.uint64), lib=lib)
+                if [int(x) if int(x) != 2**32 - 1 else -1 for x in got] != a["out"]:
+                    return False
+                got = o.rank(S, e["sigma"], np.array(r["c"]), np.array(r["i"]), lib=lib)
+                if [int(x) for x in got] != r["out"]:
+                    return False
+                got = o.select(S, e["sigma"], np.array(q["c"]), np.array(q["k"]), lib=lib)
+                if [int(x) if int(x) != 2**64 - 1 else -1 for x in got] != q["out"]:
+                    return False
         for sigma, b, n in ((256, 1, 1500), (5, 1, 100), (3000, 2, 700)):
             S = synth.zipf(n, sigma, 1.0, b, 7)
             res = o.build(S, sigma, lib=lib)

@@ -207,6 +207,22 @@ def test_tree_walk_reconstructs_and_queries(oracle_mod, sigma, b):
     assert (oracle_mod.select(S, sigma, c, np.zeros_like(cnt)) == np.uint64(2**64 - 1)).all()
 
 
+def test_query_hand_examples(oracle_mod):
+    # access / rank / select of Section 2 on hand-derived examples (rank
+    # inclusive of i, select 1-based; no answer = all ones of the width)
+    with open(os.path.join(HERE, "golden", "query_examples.json")) as f:
+        ex = json.load(f)["examples"]
+    for e in ex:
+        S = np.array(e["S"], dtype=np.uint8)
+        a, r, q = e["access"], e["rank"], e["select"]
+        got = oracle_mod.access(S, np.array(a["i"], dtype=np.uint64))
+        assert [int(x) if int(x) != 2**32 - 1 else -1 for x in got] == a["out"], e["name"]
+        got = oracle_mod.rank(S, e["sigma"], np.array(r["c"]), np.array(r["i"]))
+        assert [int(x) for x in got] == r["out"], e["name"]
+        got = oracle_mod.select(S, e["sigma"], np.array(q["c"]), np.array(q["k"]))
+        assert [int(x) if int(x) != 2**64 - 1 else -1 for x in got] == q["out"], e["name"]
+
+
 def test_edge_cases(oracle_mod):
     # n = 0: valid, empty bitmaps, a directory of one zero entry per level
     res = oracle_mod.build(np.zeros(0, dtype=np.uint8), 256)
